@@ -1,0 +1,75 @@
+"""Exact solution of the linearised problem by Fourier transform (test oracle).
+
+TEST INFRASTRUCTURE ONLY (tests/ use it to pin the nonlinear oracle in the
+small-bump limit).
+
+Sec. 4.1 linearises the problem about the uniform stream: Laplace in
+-1 < z < 0 with phi_z = zeta_x and phi_x - 1 + zeta/F^2 = 0 on z = 0 and
+phi_z = beta_x on z = -1, zeta -> 0 far upstream.  With b = beta + 1 and the
+Fourier convention q(x, y) = sum q^(a, c) exp(i(a x + c y)), the potential
+perturbation is A cosh(kz) + B sinh(kz), k = sqrt(a^2 + c^2), and the three
+conditions give (derived here from those conditions, not transcribed):
+
+    zeta^ = F^2 a^2 sech(k) b^ / (F^2 a^2 - k tanh k).
+
+This is the transfer function behind the double Fourier integral printed in
+Sec. 4.1 (its pole is the dispersion relation k F^2 = sec^2(psi) tanh k with
+a = k cos(psi)).  The radiation condition picks the contour: steady waves
+appear only downstream.  Here it is imposed by Rayleigh damping, a -> a - i mu
+in the factors that come from d/dx, and the limit mu -> 0 is approached by
+Richardson-free refinement (the tests use several mu).  The sign of the shift
+is the one that leaves the upstream side quiet (checked by the tests).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def zeta_linear(b_func, F: float, Lx: float, Ly: float, h: float, mu: float, sign: float = -1.0):
+    """Linear free surface on a periodic box [-Lx/2, Lx/2) x [-Ly/2, Ly/2) with
+    spacing h.  b_func(X, Y) is the bottom perturbation beta + 1.  Returns
+    (x, y, zeta) with zeta[j, i] at (x[i], y[j])."""
+    nx = int(round(Lx / h))
+    ny = int(round(Ly / h))
+    x = (np.arange(nx) - nx // 2) * h
+    y = (np.arange(ny) - ny // 2) * h
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    b = b_func(X, Y)
+    bh = np.fft.fft2(b)
+    a = 2.0 * np.pi * np.fft.fftfreq(nx, d=h)[None, :]
+    c = 2.0 * np.pi * np.fft.fftfreq(ny, d=h)[:, None]
+    ad = a + sign * 1j * mu
+    k = np.sqrt(a * a + c * c)
+    with np.errstate(over="ignore"):
+        sech = np.where(k < 350.0, 1.0 / np.cosh(np.minimum(k, 350.0)), 0.0)
+    th = np.tanh(k)
+    den = F * F * ad * ad - k * th
+    zh = F * F * ad * ad * sech * bh / den
+    z = np.real(np.fft.ifft2(zh))
+    return x, y, z
+
+
+def sample(x, y, z, xq, yq):
+    """Sample zeta at grid points that coincide with FFT nodes."""
+    h = x[1] - x[0]
+    i = np.rint((np.asarray(xq) - x[0]) / h).astype(int)
+    j = np.rint((np.asarray(yq) - y[0]) / h).astype(int)
+    return z[np.ix_(j, i)]
+
+
+def dispersion_k(F: float, psi: float = 0.0) -> float:
+    """Real positive root of k F^2 = sec^2(psi) tanh k (Sec. 4.1), by bisection."""
+    s2 = 1.0 / np.cos(psi) ** 2
+    f = lambda k: k * F * F - s2 * np.tanh(k)
+    lo, hi = 1e-9, 1.0
+    while f(hi) < 0.0:
+        hi *= 2.0
+    if f(lo) >= 0.0:
+        raise ValueError("no positive root (supercritical at this angle)")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
