@@ -1,0 +1,319 @@
+"""Benchmark: JFNK solve time and residual pair-evaluations/s at 181 x 61.
+
+One step = one complete Jacobian-free Newton-Krylov solve of the paper's
+collocation system (181 x 61 free-surface and bottom meshes, dx = dy = 0.3,
+Gaussian bump 0.2 exp(-(x^2+y^2)), F = 0.7) from the uniform-stream guess to
+|F|_inf <= 1e-8, in the mixed form (FP32-compensated pair sums inside the
+Jacobian-vector products, FP64 Newton residual, line search, GMRES and
+preconditioner).  The preconditioner depends only on the mesh and F and is
+factored once before the timed steps (its time is reported separately).
+
+value = pair evaluations performed by all residuals of the step / step time.
+
+--impl reference times the FP64 CPU oracle on the host cores (one full
+residual per step) in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "JFNK solve time & residual pair-evals/s at 181x61, mixed+learned vs plain FP64"
+UNIT = "pair-evals/s"
+# algorithmic work of the FP32C pair kernel per (target half point, source node)
+# index pair: 46 FP32 ALU instructions + 5 MUFU rsqrt = 51 issue slots
+INSTR_PER_INDEX_PAIR = 51
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(mesh, topo, F, u, reps: int = 1):
+    import oracle as O
+    P = O.problem(mesh, F)
+    O.residual(P, topo, u)  # load + warm
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        O.residual(P, topo, u)
+    dt = (time.perf_counter() - t0) / reps
+    return mesh.pair_evals() / dt, O.num_threads(), dt
+
+
+def run_reference(args):
+    """The oracle on the host cores, same config, metric and unit."""
+    import oracle as O
+    from paper_1709_08803_gb300 import workloads as W
+
+    O.build()
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    mesh, topo, F = W.config_paper_scale(0.7)
+    u = W.smooth_guess(mesh, 7)
+    P = O.problem(mesh, F)
+    for _ in range(args.warmup):
+        O.residual(P, topo, u)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.residual(P, topo, u)
+        times.append(time.perf_counter() - t0)
+    dt = float(np.mean(times))
+    value = mesh.pair_evals() / dt
+    sample = "one full FP64 residual of the 181x61 system per step (4.849e8 pair evaluations)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "181x61 free surface + bottom, dx=dy=0.3, bump 0.2, F=0.7; "
+                                   "oracle residual on host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--F", type=float, default=0.7)
+    ap.add_argument("--eta", type=float, default=1e-2)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import __graft_entry__
+    from paper_1709_08803_gb300 import bfs
+    from paper_1709_08803_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+
+    mesh, topo, F = W.config_paper_scale(args.F)
+    opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, eta=args.eta)
+    ctx = bfs.Context(mesh, topo, F, opts)
+    pairs_per_residual = ctx.pair_evals
+    n_index_pairs = mesh.n_targets * mesh.n_sources
+
+    t0 = time.perf_counter()
+    ctx.precond_factor()
+    torch.cuda.synchronize()
+    factor_ms = (time.perf_counter() - t0) * 1e3
+
+    u0 = ctx.flat_guess()
+    u = torch.empty_like(u0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        u.copy_(u0)
+        return ctx.solve(u)
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K device-resident solves ---------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile_read()
+    ctx.profile_enable(True)
+    _, _, _, _, launches0 = ctx.profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, evals, stats = [], 0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between steps (not timed)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = one_solve()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        stats.append(st)
+        evals += st["residual_evals_fp64"] + st["residual_evals_fp32"]
+    torch.cuda.synchronize()
+    ms64, n64, ms32, n32, launches1 = ctx.profile_read()
+    ctx.profile_enable(False)
+    clocks = sampler.stop()
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    value = world * evals * pairs_per_residual / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+    status_ok = all(s["status"] == 0 for s in stats)
+
+    # ---- end to end through the host-buffer entry point -------------------
+    u_host = np.ascontiguousarray(u0.cpu().numpy())
+    pin = torch.empty(ctx.n, dtype=torch.float64).pin_memory()
+    pin_np = pin.numpy()
+    e2e_times, e2e_evals = [], 0
+    for i in range(max(1, min(args.steps, 3))):
+        pin_np[:] = u_host
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ctx.solve_host(pin_np)
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_evals += st["residual_evals_fp64"] + st["residual_evals_fp32"]
+    e2e_value = world * e2e_evals * pairs_per_residual / sum(e2e_times)
+
+    # ---- plain FP64 solve for comparison (not in the timed region) --------
+    plain = None
+    if not args.no_plain and rank == 0:
+        ctx64 = bfs.Context(mesh, topo, F, bfs.default_options(tol=1e-8))
+        ctx64.precond_factor()
+        up = ctx64.flat_guess()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stp = ctx64.solve(up)
+        torch.cuda.synchronize()
+        plain = {"solve_ms": (time.perf_counter() - t0) * 1e3, "newton_its": stp["newton_its"],
+                 "krylov_its": stp["krylov_its"], "residual_evals_fp64": stp["residual_evals_fp64"],
+                 "fnorm_inf": stp["fnorm_inf"],
+                 "u_max_abs_diff_vs_mixed": float((up - u).abs().max().item())}
+        ctx64.close()
+
+    # ---- roofline of the dominant kernel (FP32C pair kernel) --------------
+    peaks, src = _peaks()
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tinst = sms * 128 * sm_mhz_max * 1e6 / 1e12
+    avg32 = ms32 / max(n32, 1)
+    achieved = INSTR_PER_INDEX_PAIR * n_index_pairs / (avg32 / 1e3) / 1e12 if n32 else None
+    roofline = {"bound": "alu", "kernel": "k_pairs<float> (FP32C all-pairs quadrature)",
+                "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+                "frac": (achieved / peak_tinst) if achieved else None, "traffic": None,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz (max SM clock, {src} peaks file)",
+                "avg_launch_ms": avg32, "launches": n32,
+                "fp64_pair_kernel_avg_ms": ms64 / max(n64, 1) if n64 else None,
+                "share_of_step": (ms32 + ms64) / (total_s * 1e3) if total_s else None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, cores, dt = cpu_oracle_rate(mesh, topo, F, W.smooth_guess(mesh, 7), reps=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one full FP64 oracle residual at 181x61 ({mesh.pair_evals():.3e} pair "
+                         f"evaluations, {dt:.2f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32c+f64", "data": "synthetic",
+                "config": {"workload": "181x61 free surface + bottom, dx=dy=0.3, x in [-15,39], "
+                                       "y in [-9,9], beta=-1+0.2exp(-(x^2+y^2)), F=%.2f; mixed JFNK "
+                                       "solve from the uniform stream to |F|inf<=1e-8" % F,
+                           "form": "mixed (FP32C Jv residuals, FP64 Newton/GMRES/LU), no learned guess",
+                           "l2": "flushed between steps (256 MiB write); sources fit in L2",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "precond_half_band": int(opts.half_band if opts.half_band > 0 else max(1, round(mesh.M / 20))),
+                           "precond_factor_ms_untimed": factor_ms},
+                "solve": {"newton_its": stats[-1]["newton_its"], "krylov_its": stats[-1]["krylov_its"],
+                          "residual_evals_fp64": stats[-1]["residual_evals_fp64"],
+                          "residual_evals_fp32": stats[-1]["residual_evals_fp32"],
+                          "fnorm_inf": stats[-1]["fnorm_inf"], "all_converged": status_ok,
+                          "step_ms": step_ms},
+                "plain_fp64": plain,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * ctx.n,
+                        "d2h_bytes_per_step": 8 * ctx.n, "entry": "bfs_solve_host",
+                        "steps": len(e2e_times)},
+                "gpu_launches": int(launches1 - launches0),
+                "clocks": clocks}
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

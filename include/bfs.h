@@ -1,0 +1,190 @@
+/*
+ * bfs.h -- C ABI of the GB300 boundary-integral JFNK solver for steady 3-D
+ * free-surface flow over bottom topography (Buttle, Pethiyagoda, Moroney &
+ * McCue, arXiv:1709.08803).
+ *
+ * Conventions shared by every call:
+ *   - Return value: BFS_OK (0) on success, a negative BFS_E* code otherwise.
+ *     No exception crosses the ABI.  bfs_last_error(ctx) gives a message for
+ *     the last failing call on ctx (bfs_last_error(NULL) for bfs_setup).
+ *   - Vectors of unknowns u and residuals F are FP64 arrays of length
+ *     n = 3(N+1)M (bfs_n_unknowns).
+ *       u, per slice j = 1..M, for q = zeta, then phi, then psi (three blocks
+ *       of (N+1)M):  [ q(x1, y_j), q_x(x_1, y_j), ..., q_x(x_N, y_j) ]
+ *       (Sec. 3.1, the vector of unknowns).
+ *       F, per slice l, in three blocks: [F5, F6, F1(1..N-1)],
+ *       [F3, F4, F2(1..N-1)], [F8, F9, F7(1..N-1)]  (App. B, the order of the
+ *       vector function): F1 the combined dynamic condition (Sec. 2.1), F2
+ *       and F7 the boundary integral equation collocated at the half mesh
+ *       points of the free surface and of the bottom (Sec. 2.2, 3.1), F3-F6,
+ *       F8, F9 the radiation conditions of Scullen (Sec. 3.1).
+ *   - Pointers called "device" must be CUDA device memory of the current
+ *     device (e.g. torch tensor data_ptr()); "host" pointers are ordinary
+ *     host memory.  The caller owns every buffer it passes; the context owns
+ *     all the memory it allocates and frees it in bfs_destroy.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that take a stream are asynchronous on it unless stated otherwise.
+ *   - A context is used from one host thread and one stream at a time.
+ */
+#ifndef BFS_H
+#define BFS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BFS_OK = 0,
+    BFS_EINVAL = -1,      /* invalid argument (sizes, spacing, F, topography) */
+    BFS_ECUDA = -2,       /* a CUDA runtime call failed */
+    BFS_ENOMEM = -3,      /* device allocation failed */
+    BFS_ENAN = -4,        /* a residual or update was not finite */
+    BFS_ENOCONV = -5,     /* Newton iteration limit reached */
+    BFS_ELINESEARCH = -6, /* line search found no sufficient decrease */
+    BFS_EBREAKDOWN = -7,  /* GMRES breakdown without convergence */
+    BFS_ESINGULAR = -8,   /* zero pivot while factoring the preconditioner */
+    BFS_ENOPREC = -9,     /* preconditioner applied before it was factored */
+    BFS_ETIMEOUT = -10    /* wall-clock budget of bfs_solve exhausted */
+};
+
+/* Arithmetic of the boundary-integral pair sums. */
+enum {
+    BFS_FP64 = 0,  /* FP64 throughout */
+    BFS_FP32C = 1  /* pair terms in FP32 with compensated (two-sum) accumulation,
+                      reduced and finished in FP64 */
+};
+
+/* Truncated mesh x_i = x1 + (i-1) dx, i = 1..N; y_j = y1 + (j-1) dy, j = 1..M
+   (Sec. 3.1).  half_domain = 1 solves only y >= 0 (y1 must be 0) for flows
+   symmetric in y: the rows j >= 2 are mirrored to y < 0 as extra sources. */
+typedef struct {
+    int N, M;
+    int half_domain;
+    double x1, y1, dx, dy;
+} bfs_mesh;
+
+/* Bottom z = beta(x, y) and its exact derivatives at the N*M nodes, index
+   i + N*j (0-based), HOST arrays, copied by bfs_setup.  beta must stay below
+   the undisturbed surface (beta < 0) and tend to -1 far away (Sec. 2.1). */
+typedef struct {
+    const double *beta, *beta_x, *beta_y;
+} bfs_topo;
+
+typedef struct {
+    double n_rad;         /* radiation decay rate n (Sec. 3.1; 0.05) */
+    double sign_I4;       /* sign of the bottom single layer I4: -1 from Green's
+                             identity with outward normals (default), +1 as printed */
+    int half_band;        /* preconditioner half band width in slices (App. A) */
+    double tol;           /* bfs_solve stops when |F|_inf <= tol */
+    int gmres_restart;    /* Krylov vectors per GMRES cycle */
+    int max_newton;       /* Newton iteration limit */
+    int max_krylov;       /* Krylov iterations per Newton step */
+    double eta;           /* GMRES relative tolerance (forcing term) */
+    int krylov_precision; /* BFS_FP64 or BFS_FP32C for the residuals inside
+                             the Jacobian-vector products; the Newton residual
+                             and the line search are always FP64 */
+    double jv_h_rel;      /* FD step: h = jv_h_rel (1 + |u|_2) / |z|_2; <= 0 picks
+                             sqrt(eps) of the Krylov precision's arithmetic */
+    double time_budget_s; /* bfs_solve wall-clock limit (<= 0: none) */
+    int src_splits;       /* source splits of the pair kernels (<= 0: automatic) */
+} bfs_options;
+
+typedef struct {
+    int newton_its, krylov_its;
+    int residual_evals_fp64, residual_evals_fp32;
+    int precond_applies;
+    double fnorm_inf, fnorm_2; /* of the final FP64 residual */
+    double seconds;            /* wall time of bfs_solve */
+    double seconds_residual, seconds_precond, seconds_krylov_other;
+    int status;                /* same as the return value */
+} bfs_stats;
+
+typedef struct bfs_ctx bfs_ctx;
+
+/* Fills *o with the defaults (n = 0.05, sign_I4 = -1, half_band =
+   max(1, round(M/20)), tol = 1e-8, restart 50, 60 Newton steps, 200 Krylov
+   iterations, eta = 1e-4, FP64 Krylov residuals). */
+void bfs_default_options(bfs_options *o);
+
+/* Validates the problem, allocates device memory on the current device,
+   uploads the topography and precomputes the parts of the bottom integral
+   that depend only on the bottom (the single-layer sum over the bottom seen
+   from bottom collocation points, Sec. 3.1).  Synchronous.  Errors:
+   BFS_EINVAL for N < 4, M < 3, dx or dy <= 0, F <= 0, half_domain with
+   y1 != 0, beta >= 0 anywhere or a non-finite input; BFS_ENOMEM; BFS_ECUDA. */
+int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_options *opt,
+              bfs_ctx **out);
+
+void bfs_destroy(bfs_ctx *ctx);
+const char *bfs_last_error(const bfs_ctx *ctx);
+int bfs_n_unknowns(const bfs_ctx *ctx);
+/* Pair evaluations of one residual: 4 (N-1)M x (number of sources). */
+double bfs_pair_evals(const bfs_ctx *ctx);
+
+/* Fu = F(u), the nonlinear residual (Sec. 3.1; App. B order).  u, Fu: device,
+   length n.  precision: BFS_FP64 or BFS_FP32C.  Asynchronous; a non-finite
+   entry raises the context's NaN flag (read by bfs_check_finite). */
+int bfs_residual(bfs_ctx *ctx, const double *u, double *Fu, int precision, void *stream);
+
+/* Synchronises stream and returns BFS_ENAN if any residual evaluated since the
+   previous call was non-finite, else BFS_OK; clears the flag. */
+int bfs_check_finite(bfs_ctx *ctx, void *stream);
+
+/* Jz = (F(u + h z) - Fu) / h, the finite-difference Jacobian-vector product
+   (Sec. 3.2).  u, Fu, z, Jz: device, length n; Fu must be F(u) in FP64.
+   h <= 0 picks h = h_rel (1 + |u|_2) / |z|_2 on the device.  The perturbed
+   residual uses `precision`.  Jz = 0 when z = 0. */
+int bfs_jvp(bfs_ctx *ctx, const double *u, const double *Fu, const double *z, double *Jz,
+            double h, int precision, void *stream);
+
+/* Forms the Jacobian of the linearised discrete system (Sec. 4.2, App. B),
+   keeps the slice blocks within half_band of the diagonal (App. A), reorders
+   it slice by slice into 3(N+1) x 3(N+1) blocks and factors it by block LU
+   with partial pivoting inside each diagonal block.  Depends on the mesh, F
+   and n only.  half_band < 0 uses the option's value.  Synchronous.
+   Errors: BFS_ESINGULAR, BFS_ENOMEM, BFS_ECUDA. */
+int bfs_precond_factor(bfs_ctx *ctx, int half_band, void *stream);
+
+/* z = P^{-1} r with the factored preconditioner.  r, z: device, length n,
+   in the order of u (r may equal z).  BFS_ENOPREC before bfs_precond_factor. */
+int bfs_precond_apply(bfs_ctx *ctx, const double *r, double *z, void *stream);
+
+/* Damped inexact Newton with backtracking line search and right-
+   preconditioned restarted GMRES on finite-difference Jacobian-vector
+   products (Sec. 3.2), in place on the device vector u_inout (length n).
+   Factors the preconditioner first if needed.  Synchronous; st may be NULL.
+   Returns BFS_OK when |F|_inf <= tol, else BFS_ENOCONV, BFS_ELINESEARCH,
+   BFS_EBREAKDOWN, BFS_ENAN or BFS_ETIMEOUT (u_inout then holds the last
+   accepted iterate). */
+int bfs_solve(bfs_ctx *ctx, double *u_inout, bfs_stats *st, void *stream);
+
+/* bfs_solve on a HOST vector: copies u_host to the device, solves and copies
+   the result back (both copies inside the call).  Synchronous. */
+int bfs_solve_host(bfs_ctx *ctx, double *u_host_inout, bfs_stats *st, void *stream);
+
+/* bfs_residual on HOST vectors (copies in and out inside the call). Synchronous. */
+int bfs_residual_host(bfs_ctx *ctx, const double *u_host, double *F_host, int precision,
+                      void *stream);
+
+/* Writes the uniform-stream guess (zeta = 0, phi = psi = x) into the device
+   vector u (length n). */
+int bfs_flat_guess(bfs_ctx *ctx, double *u, void *stream);
+
+/* Nodal fields from u (device in, device out): out holds 8 arrays of N*M
+   (index i + N*j): zeta, zeta_x, zeta_y, phi, phi_x, phi_y, psi, psi_x
+   (trapezoid reconstruction in x, second-order differences in y). */
+int bfs_unpack(bfs_ctx *ctx, const double *u, double *out, void *stream);
+
+/* Profiling.  bfs_profile_enable(ctx, 1) records a CUDA event pair on the
+   launching stream around every pair-kernel launch of the context;
+   bfs_profile_read waits for the recorded events and returns, in out4,
+   {total ms FP64 pair kernels, their launch count, total ms FP32C pair
+   kernels, their launch count}, then forgets them.  *launches (optional)
+   receives the number of kernels the context has launched since bfs_setup. */
+int bfs_profile_enable(bfs_ctx *ctx, int on);
+int bfs_profile_read(bfs_ctx *ctx, double *out4, unsigned long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFS_H */

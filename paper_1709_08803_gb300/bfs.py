@@ -1,0 +1,250 @@
+"""Python binding of libbfs (include/bfs.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy /
+torch arguments to pointers and status codes to exceptions.  It raises
+immediately if libbfs.so is missing or CUDA is unavailable: there is no CPU
+fallback.  Device buffers are torch CUDA tensors (torch is used for device
+memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfs.so")
+
+BFS_OK, BFS_EINVAL, BFS_ECUDA, BFS_ENOMEM, BFS_ENAN = 0, -1, -2, -3, -4
+BFS_ENOCONV, BFS_ELINESEARCH, BFS_EBREAKDOWN, BFS_ESINGULAR = -5, -6, -7, -8
+BFS_ENOPREC, BFS_ETIMEOUT = -9, -10
+BFS_FP64, BFS_FP32C = 0, 1
+STATUS_NAMES = {0: "BFS_OK", -1: "BFS_EINVAL", -2: "BFS_ECUDA", -3: "BFS_ENOMEM", -4: "BFS_ENAN",
+                -5: "BFS_ENOCONV", -6: "BFS_ELINESEARCH", -7: "BFS_EBREAKDOWN",
+                -8: "BFS_ESINGULAR", -9: "BFS_ENOPREC", -10: "BFS_ETIMEOUT"}
+
+
+class BfsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bfs_mesh(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("half_domain", ctypes.c_int),
+                ("x1", ctypes.c_double), ("y1", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
+
+
+class bfs_topo(ctypes.Structure):
+    _fields_ = [("beta", ctypes.POINTER(ctypes.c_double)),
+                ("beta_x", ctypes.POINTER(ctypes.c_double)),
+                ("beta_y", ctypes.POINTER(ctypes.c_double))]
+
+
+class bfs_options(ctypes.Structure):
+    _fields_ = [("n_rad", ctypes.c_double), ("sign_I4", ctypes.c_double),
+                ("half_band", ctypes.c_int), ("tol", ctypes.c_double),
+                ("gmres_restart", ctypes.c_int), ("max_newton", ctypes.c_int),
+                ("max_krylov", ctypes.c_int), ("eta", ctypes.c_double),
+                ("krylov_precision", ctypes.c_int), ("jv_h_rel", ctypes.c_double),
+                ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int)]
+
+
+class bfs_stats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("krylov_its", ctypes.c_int),
+                ("residual_evals_fp64", ctypes.c_int), ("residual_evals_fp32", ctypes.c_int),
+                ("precond_applies", ctypes.c_int),
+                ("fnorm_inf", ctypes.c_double), ("fnorm_2", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("seconds_residual", ctypes.c_double),
+                ("seconds_precond", ctypes.c_double), ("seconds_krylov_other", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libbfs.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libbfs.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        C = ctypes.POINTER
+        L.bfs_default_options.argtypes = [C(bfs_options)]
+        L.bfs_setup.argtypes = [C(bfs_mesh), C(bfs_topo), ctypes.c_double, C(bfs_options), C(_VP)]
+        L.bfs_destroy.argtypes = [_VP]
+        L.bfs_last_error.argtypes = [_VP]
+        L.bfs_last_error.restype = ctypes.c_char_p
+        L.bfs_n_unknowns.argtypes = [_VP]
+        L.bfs_pair_evals.argtypes = [_VP]
+        L.bfs_pair_evals.restype = ctypes.c_double
+        L.bfs_residual.argtypes = [_VP, _VP, _VP, ctypes.c_int, _VP]
+        L.bfs_check_finite.argtypes = [_VP, _VP]
+        L.bfs_jvp.argtypes = [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int, _VP]
+        L.bfs_precond_factor.argtypes = [_VP, ctypes.c_int, _VP]
+        L.bfs_precond_apply.argtypes = [_VP, _VP, _VP, _VP]
+        L.bfs_solve.argtypes = [_VP, _VP, C(bfs_stats), _VP]
+        L.bfs_solve_host.argtypes = [_VP, _VP, C(bfs_stats), _VP]
+        L.bfs_residual_host.argtypes = [_VP, _VP, _VP, ctypes.c_int, _VP]
+        L.bfs_flat_guess.argtypes = [_VP, _VP, _VP]
+        L.bfs_unpack.argtypes = [_VP, _VP, _VP, _VP]
+        L.bfs_profile_enable.argtypes = [_VP, ctypes.c_int]
+        L.bfs_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_ulonglong)]
+        _lib = L
+    return _lib
+
+
+def default_options(**kw) -> bfs_options:
+    o = bfs_options()
+    lib().bfs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A problem set up on the current CUDA device (wraps bfs_ctx)."""
+
+    def __init__(self, mesh, topo, F: float, options: bfs_options | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA device required: libbfs has no CPU path")
+        self.mesh = mesh
+        self._h = [np.ascontiguousarray(a, dtype=np.float64) for a in (topo.beta, topo.beta_x, topo.beta_y)]
+        m = bfs_mesh(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy)
+        D = ctypes.POINTER(ctypes.c_double)
+        t = bfs_topo(*[a.ctypes.data_as(D) for a in self._h])
+        self.options = options if options is not None else default_options()
+        ctx = _VP()
+        rc = lib().bfs_setup(ctypes.byref(m), ctypes.byref(t), float(F), ctypes.byref(self.options),
+                             ctypes.byref(ctx))
+        if rc != BFS_OK:
+            raise BfsError(rc, lib().bfs_last_error(None).decode())
+        self._ctx = ctx
+        self.n = lib().bfs_n_unknowns(ctx)
+        self.pair_evals = lib().bfs_pair_evals(ctx)
+
+    def _check(self, rc):
+        if rc != BFS_OK:
+            raise BfsError(rc, lib().bfs_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().bfs_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, t):
+        import torch
+        assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+        assert t.is_contiguous() and t.numel() == self.n, "expected a contiguous float64 CUDA vector of length n"
+        return ctypes.c_void_p(_ptr(t))
+
+    # --- the C ABI, one method per entry point -----------------------------
+    def residual(self, u, out=None, precision: int = BFS_FP64, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(u)
+        self._check(lib().bfs_residual(self._ctx, self._vec(u), self._vec(out), precision, _stream(stream)))
+        return out
+
+    def check_finite(self, stream=None) -> bool:
+        rc = lib().bfs_check_finite(self._ctx, _stream(stream))
+        if rc == BFS_ENAN:
+            return False
+        self._check(rc)
+        return True
+
+    def jvp(self, u, Fu, z, out=None, h: float = 0.0, precision: int = BFS_FP64, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(u)
+        self._check(lib().bfs_jvp(self._ctx, self._vec(u), self._vec(Fu), self._vec(z), self._vec(out),
+                                  float(h), precision, _stream(stream)))
+        return out
+
+    def precond_factor(self, half_band: int = -1, stream=None):
+        self._check(lib().bfs_precond_factor(self._ctx, int(half_band), _stream(stream)))
+
+    def precond_apply(self, r, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(r)
+        self._check(lib().bfs_precond_apply(self._ctx, self._vec(r), self._vec(out), _stream(stream)))
+        return out
+
+    def solve(self, u, stream=None, raise_on_error: bool = True):
+        st = bfs_stats()
+        rc = lib().bfs_solve(self._ctx, self._vec(u), ctypes.byref(st), _stream(stream))
+        if raise_on_error:
+            self._check(rc)
+        return st.as_dict()
+
+    def solve_host(self, u_host: np.ndarray, stream=None, raise_on_error: bool = True):
+        assert u_host.dtype == np.float64 and u_host.flags.c_contiguous and u_host.size == self.n
+        st = bfs_stats()
+        rc = lib().bfs_solve_host(self._ctx, ctypes.c_void_p(u_host.ctypes.data), ctypes.byref(st),
+                                  _stream(stream))
+        if raise_on_error:
+            self._check(rc)
+        return st.as_dict()
+
+    def residual_host(self, u_host: np.ndarray, out: np.ndarray | None = None,
+                      precision: int = BFS_FP64, stream=None):
+        assert u_host.dtype == np.float64 and u_host.flags.c_contiguous and u_host.size == self.n
+        if out is None:
+            out = np.empty(self.n)
+        self._check(lib().bfs_residual_host(self._ctx, ctypes.c_void_p(u_host.ctypes.data),
+                                            ctypes.c_void_p(out.ctypes.data), precision, _stream(stream)))
+        return out
+
+    def flat_guess(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        self._check(lib().bfs_flat_guess(self._ctx, self._vec(out), _stream(stream)))
+        return out
+
+    def profile_enable(self, on: bool = True):
+        self._check(lib().bfs_profile_enable(self._ctx, int(bool(on))))
+
+    def profile_read(self):
+        """Returns (ms_fp64, launches_fp64, ms_fp32c, launches_fp32c, kernel_launches)."""
+        out = (ctypes.c_double * 4)()
+        n = ctypes.c_ulonglong()
+        self._check(lib().bfs_profile_read(self._ctx, out, ctypes.byref(n)))
+        return out[0], int(out[1]), out[2], int(out[3]), int(n.value)
+
+    def unpack(self, u, stream=None):
+        import torch
+        NM = self.mesh.N * self.mesh.M
+        out = torch.empty(8 * NM, dtype=torch.float64, device="cuda")
+        self._check(lib().bfs_unpack(self._ctx, self._vec(u), ctypes.c_void_p(_ptr(out)), _stream(stream)))
+        names = ("zeta", "zeta_x", "zeta_y", "phi", "phi_x", "phi_y", "psi", "psi_x")
+        return {k: out[i * NM:(i + 1) * NM].view(self.mesh.M, self.mesh.N) for i, k in enumerate(names)}

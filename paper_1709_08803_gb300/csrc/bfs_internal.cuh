@@ -1,0 +1,138 @@
+// Internal declarations of the GB300 boundary-integral JFNK library.
+// Everything here is private to libbfs; the public ABI is include/bfs.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bfs.h"
+
+namespace bfs {
+
+// Per-source record (16 values, FP64 or FP32).  Lengths are in units of dx,
+// measured from the mesh centre, so that horizontal offsets between nodes
+// and half points are exact in FP32 when dx == dy.
+//   0 xs   1 ys   2 zeta/dx   3 (beta+1)/dx
+//   4 zeta_x  5 zeta_y  6 beta_x  7 beta_y
+//   8 w1 f   9 w2 zeta_x   10 w1 g   11 w2 sigma beta_x
+//   12 w1    13 w2   14,15 unused
+// with f = phi - x, g = psi - x, w the trapezoid weight, w1 = w/dx^2 (double
+// layer, K1 scales as 1/dx^2) and w2 = w/dx (single layer and S2).
+constexpr int REC = 16;
+
+// Per-target record (16 values) for the half point (k, l):
+//   0 xt  1 yt  2 zeta*/dx  3 (beta*+1)/dx  4 zeta_x*  5 zeta_y*  6 f*  7 g*
+//   8 A  9 B  10 C   (S2 coefficients of the free surface at the target)
+//   11 zeta*/dx + 1/dx   12 (beta*+1)/dx - 1/dx   13 phi_x*  14 phi_y*  15 unused
+constexpr int TREC = 16;
+
+// Accumulators written by the pair kernels, per split and target:
+//   0  double layer at top targets (top and bottom sheets)
+//   1  single layer at top targets (top and bottom sheets)
+//   2  sum of w S2 at top targets
+//   3  double layer at bottom targets (top and bottom sheets)
+//   4  single layer of the top sheet at bottom targets
+constexpr int NACC = 5;
+
+struct PairPlan {
+    int tpb;        // threads per CTA
+    int tpt;        // targets per thread
+    int chunk;      // sources staged per shared-memory chunk
+    int splits;     // source splits (grid.y)
+    int per_split;  // sources per split (multiple of chunk)
+    int tiles;      // target tiles (grid.x)
+};
+
+}  // namespace bfs
+
+struct bfs_ctx {
+    // problem
+    int N, M, half;
+    double x1, y1, dx, dy, F;
+    bfs_options opt;
+    int n, Nt, NM, Ns, Ns_cap;
+    double xc, yc;  // centre of the mesh (physical)
+    int device;
+
+    // residual buffers
+    double *d_beta, *d_bx, *d_by;  // NM each
+    double *d_nodal;               // 8 NM: zeta, zx, zy, phi, phx, phy, psi, psx
+    double *d_src64;               // Ns_cap * REC
+    float *d_src32;                // Ns_cap * REC
+    double *d_tgt64;               // Nt * TREC
+    float *d_tgt32;                // Nt * TREC
+    double *d_part;                // max splits * NACC * Nt
+    double *d_constB;              // Nt: bottom-only single-layer part at bottom targets
+    int *d_flag;                   // non-finite flag
+    bfs::PairPlan plan64, plan32;
+    size_t part_cap;
+
+    // Jacobian-vector product scratch
+    double *d_up, *d_Fp;  // n each
+    double *d_scal;       // 16 scalars
+
+    // Newton / GMRES workspace
+    int m_alloc;
+    double *d_V;      // (m+1) n Krylov basis
+    double *d_H;      // Hessenberg, column j at d_H + j (m+1)
+    double *d_giv;    // cs[m], sn[m], g[m+1], y[m], h[m+1], h2[m+1]
+    double *d_red;    // reduction partials
+    double *d_sbase;  // one allocation holding the n-vectors below
+    double *d_F, *d_du, *d_ut, *d_Ft, *d_z, *d_w, *d_F32, *d_uio;  // n each
+    double *h_pin;    // pinned host scalars
+
+    // preconditioner
+    int pc_ready, pc_h, nb;
+    double *d_pc;      // M * (2h+1) * nb * nb  block-banded factors
+    double *d_gj;      // 2 * nb * 2nb  Gauss-Jordan ping-pong
+    double *d_rowsum5; // Nt
+    int *d_pivflag;
+    double *d_perm_a, *d_perm_b;  // n each
+
+    // profiling: launch counter and CUDA-event timing of the pair kernels
+    unsigned long long launches;
+    int prof_on;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;  // per recorded pair: 0 FP64, 1 FP32C
+    size_t ev_used;
+
+    std::string err;
+};
+
+namespace bfs {
+
+// residual.cu
+int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cudaStream_t s);
+int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s);
+int constB_launch(bfs_ctx *c, cudaStream_t s);
+PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, int sms);
+void plans_for(int Nt, int Ns, int splits_req, int sms, PairPlan *p64, PairPlan *p32);
+
+// solver.cu
+int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
+               double h, int precision, cudaStream_t s);
+int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s);
+int alloc_solver(bfs_ctx *c);
+void norms_launch(bfs_ctx *c, const double *v, int n, double *d_out2, double *d_outinf, cudaStream_t s);
+
+// precond.cu
+int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s);
+int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s);
+void precond_free(bfs_ctx *c);
+
+int num_sms(int device);
+// records an event pair around a pair-kernel launch when profiling is on
+cudaEvent_t prof_event(bfs_ctx *c);
+}  // namespace bfs
+
+#define BFS_CUDA_TRY(ctx, call)                                                      \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return BFS_ECUDA;                                                        \
+        }                                                                            \
+    } while (0)

@@ -1,0 +1,529 @@
+// Block-banded preconditioner P = banded Jacobian of the linearised discrete
+// system (Buttle et al., arXiv:1709.08803, Sec. 4.2 and App. A, B).
+//
+// Layout.  Unknowns and equations are regrouped slice by slice: slice l owns
+// the nb = 3(N+1) unknowns [zeta(1), zeta_x(1..N) | phi(1), phi_x | psi(1), psi_x]
+// and the nb equations [F5, F6, F1(1..N-1) | F3, F4, F2 | F8, F9, F7].  P is then
+// an M x M block matrix of nb x nb blocks; App. A keeps the blocks within
+// half_band h of the diagonal, so block row l stores blocks l-h .. l+h at
+// d_pc + (l (2h+1) + (m - l + h)) nb^2 (row-major).
+//
+// Entries (derived by differentiating the linear residual of App. B; every
+// kernel there is a function of horizontal distance only, and the linear
+// Jacobian does not depend on u, on the topography or on the sign of I4):
+//   F1 = phi_x* + zeta*/F^2 - 1, F2 and F7 the linear boundary integral
+//   equation with K5 = 1/r, K6 = (r^2+1)^(-3/2), K7 = (r^2+1)^(-1/2), and the
+//   radiation rows.  Nodal values follow from q(1) and q_x by the trapezoid
+//   rule, T(i, n) being the weight of q_x(n) in q(i); half-point values are
+//   means of the two neighbouring nodes, H(k, n) = (T(k,n) + T(k+1,n)) / 2.
+//
+// Factorisation (no pivoting across blocks; partial pivoting inside the
+// diagonal blocks by Gauss-Jordan inversion):
+//   for k: D_k^-1;  W_kj = D_k^-1 U_kj;  S_ij -= S_ik W_kj;  L_ik = S_ik D_k^-1
+// stored in place: diagonal slot D_k^-1, lower slots L, upper slots W, so that
+//   forward  y_k = x_k - sum_i L_ki y_i
+//   backward z_k = D_k^-1 y_k - sum_j W_kj z_j.
+#include <math.h>
+
+#include <vector>
+
+#include "bfs_internal.cuh"
+
+namespace bfs {
+
+__device__ __forceinline__ double trap_T(int i, int n)  // 1-based
+{
+    if (i == 1) return 0.0;
+    if (n == 1) return 0.5;
+    if (n < i) return 1.0;
+    if (n == i) return 0.5;
+    return 0.0;
+}
+
+__device__ __forceinline__ double half_H(int k, int n) { return 0.5 * (trap_T(k, n) + trap_T(k + 1, n)); }
+
+__device__ double rect_S2_pc(double s1, double s2, double t1, double t2);
+
+struct PcArgs {
+    int N, M, half, h, nb;
+    double x1, y1, dx, dy, F, n_rad, xhi, ylo, yhi;
+};
+
+__device__ __forceinline__ double trap_w(const PcArgs &a, int i, int j)  // 0-based
+{
+    double cx = (i == 0 || i == a.N - 1) ? 0.5 : 1.0;
+    double cy = a.half ? ((j == a.M - 1) ? 0.5 : 1.0) : ((j == 0 || j == a.M - 1) ? 0.5 : 1.0);
+    return a.dx * a.dy * cx * cy;
+}
+
+// Closed-form integral of 1/r over the mesh rectangle seen from (xs, ys)
+// (the A = C = 1, B = 0 case of the S2 integral of Sec. 3.1).
+__device__ double g_K5(double s, double t)
+{
+    double r = sqrt(s * s + t * t), g = 0.0;
+    if (t != 0.0) g += t * ((s >= 0.0) ? log(s + r) : (log(t * t) - log(r - s)));
+    if (s != 0.0) g += s * ((t >= 0.0) ? log(t + r) : (log(s * s) - log(r - t)));
+    return g;
+}
+
+__device__ double rect_S2_pc(double s1, double s2, double t1, double t2)
+{
+    return g_K5(s2, t2) - g_K5(s1, t2) - g_K5(s2, t1) + g_K5(s1, t1);
+}
+
+// Row sums of w K5 over all nodes (and images) minus the closed-form integral:
+// the coefficient of zeta_x* in the linear F2.
+__global__ void k_rowsum5(PcArgs a, double *out)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int Nt = (a.N - 1) * a.M;
+    if (e >= Nt) return;
+    int k = e % (a.N - 1), l = e / (a.N - 1);
+    double xs = a.x1 + (k + 0.5) * a.dx, ys = a.y1 + l * a.dy;
+    double acc = 0.0;
+    for (int img = 0; img < (a.half ? 2 : 1); img++)
+        for (int j = (img ? 1 : 0); j < a.M; j++) {
+            double t = (img ? -1.0 : 1.0) * (a.y1 + j * a.dy) - ys;
+            for (int i = 0; i < a.N; i++) {
+                double s = a.x1 + i * a.dx - xs;
+                acc += trap_w(a, i, j) * rsqrt(s * s + t * t);
+            }
+        }
+    out[e] = acc - rect_S2_pc(a.x1 - xs, a.xhi - xs, a.ylo - ys, a.yhi - ys);
+}
+
+// Dense entries of block (l, m): one CTA per (l, d, k), threads over source nodes n.
+__global__ void k_form_dense(PcArgs a, double *pc, const double *rowsum5)
+{
+    extern __shared__ double sh[];  // W6[N], suffix[N+1]
+    const int N = a.N, NB = a.N + 1, nb = a.nb, h = a.h;
+    const int k0 = blockIdx.x, d = blockIdx.y, l = blockIdx.z;
+    const int m = l + d - h;
+    if (m < 0 || m >= a.M) return;
+    double *W6 = sh, *suf = sh + N;
+    double *blk = pc + ((size_t)l * (2 * h + 1) + d) * nb * nb;
+    const double xs = a.x1 + (k0 + 0.5) * a.dx, ys = a.y1 + l * a.dy;
+    const double ym = a.y1 + m * a.dy;
+    const bool img = a.half && m >= 1;
+    const size_t r2 = (size_t)(1 * NB + 2 + k0) * nb, r7 = (size_t)(2 * NB + 2 + k0) * nb;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double s = a.x1 + i * a.dx - xs, w = trap_w(a, i, m);
+        double t1 = ym - ys, p1 = s * s + t1 * t1;
+        double k5 = rsqrt(p1), k7 = rsqrt(p1 + 1.0), k6 = k7 * k7 * k7;
+        if (img) {
+            double t2 = -ym - ys, p2 = s * s + t2 * t2;
+            double q7 = rsqrt(p2 + 1.0);
+            k5 += rsqrt(p2);
+            k7 += q7;
+            k6 += q7 * q7 * q7;
+        }
+        double v5 = w * k5;
+        if (l == m && (i == k0 || i == k0 + 1)) v5 -= 0.5 * rowsum5[l * (N - 1) + k0];
+        blk[r2 + 0 * NB + 1 + i] = v5;     // dF2 / d zeta_x(i)
+        blk[r7 + 0 * NB + 1 + i] = w * k7;  // dF7 / d zeta_x(i)
+        W6[i] = w * k6;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // suffix sums of w K6 along the slice
+        double acc = 0.0;
+        suf[N] = 0.0;
+        for (int i = N - 1; i >= 0; i--) { acc += W6[i]; suf[i] = acc; }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+        double v;
+        if (i == 0) v = suf[0];  // d / d psi(1): every node carries psi(1)
+        else {
+            int n0 = i - 1;
+            if (n0 == 0) v = 0.5 * a.dx * suf[1];
+            else if (n0 < N - 1) v = a.dx * (0.5 * W6[n0] + suf[n0 + 1]);
+            else v = 0.5 * a.dx * W6[N - 1];
+        }
+        blk[r2 + 2 * NB + i] = v;  // dF2 / d psi
+        blk[r7 + 1 * NB + i] = v;  // dF7 / d phi  (equal blocks, Sec. 4.2)
+    }
+}
+
+// Sparse entries of the diagonal block of slice l: one thread per row.
+__global__ void k_form_sparse(PcArgs a, double *pc)
+{
+    const int NB = a.N + 1, nb = a.nb, h = a.h;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.M * nb) return;
+    int l = e / nb, r = e % nb;
+    double *row = pc + ((size_t)l * (2 * h + 1) + h) * nb * nb + (size_t)r * nb;
+    int grp = r / NB, rr = r % NB;
+    const double x1 = a.x1, n = a.n_rad, dx = a.dx, F2 = a.F * a.F;
+    const double TWO_PI = 6.283185307179586476925286766559;
+    int f = grp;  // radiation rows act on the group's own field
+    if (rr == 0) {
+        row[f * NB + 0] = n;
+        row[f * NB + 1] = x1;
+        return;
+    }
+    if (rr == 1) {
+        row[f * NB + 1] = n - x1 / dx;
+        row[f * NB + 2] = x1 / dx;
+        return;
+    }
+    int k = rr - 1;  // 1-based collocation index
+    if (grp == 0) {  // F1 = phi_x* + zeta*/F^2 - 1
+        row[0] = 1.0 / F2;
+        for (int p = 1; p <= a.N; p++) row[p] = dx * half_H(k, p) / F2;
+        row[NB + k] = 0.5;
+        row[NB + k + 1] = 0.5;
+    } else {  // F2 (phi) or F7 (psi): -2 pi (q* - x*)
+        row[f * NB + 0] = -TWO_PI;
+        for (int p = 1; p <= a.N; p++) row[f * NB + p] = -TWO_PI * dx * half_H(k, p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inversion with partial pivoting of one nb x nb block, one launch
+// per pivot column on ping-pong buffers X = [D | I] (nb x 2nb, row-major).
+// ---------------------------------------------------------------------------
+constexpr int GJ_ROWS = 4;
+
+__global__ void k_gj_load(const double *__restrict__ D, double *__restrict__ X, int nb)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * 2 * nb;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(e / (2 * nb)), c = (int)(e % (2 * nb));
+        X[e] = c < nb ? D[(size_t)r * nb + c] : (c - nb == r ? 1.0 : 0.0);
+    }
+}
+
+__global__ void k_gj_step(const double *__restrict__ Xi, double *__restrict__ Xo, int nb, int c,
+                          int *flag)
+{
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    __shared__ int piv;
+    __shared__ double pval;
+    const int ld = 2 * nb;
+    // pivot search in column c, rows c..nb-1 (every CTA, same order -> same answer)
+    double best = -1.0;
+    int bidx = c;
+    for (int r = c + threadIdx.x; r < nb; r += blockDim.x) {
+        double v = fabs(Xi[(size_t)r * ld + c]);
+        if (v > best) { best = v; bidx = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bidx, o);
+        if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = bv[0];
+        int i = bi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+            if (bv[w] > b || (bv[w] == b && bi[w] < i)) { b = bv[w]; i = bi[w]; }
+        piv = i;
+        pval = Xi[(size_t)i * ld + c];
+        if (!(b > 0.0) && blockIdx.x == 0) atomicOr(flag, 1);
+    }
+    __syncthreads();
+    const int p = piv;
+    const double ip = pval != 0.0 ? 1.0 / pval : 0.0;
+    const int r0 = blockIdx.x * GJ_ROWS;
+    for (int rr = 0; rr < GJ_ROWS; rr++) {
+        int r = r0 + rr;
+        if (r >= nb) break;
+        int src = (r == c) ? p : ((r == p) ? c : r);
+        const double *xs = Xi + (size_t)src * ld;
+        const double *xp = Xi + (size_t)p * ld;
+        double *xo = Xo + (size_t)r * ld;
+        if (r == c) {
+            for (int q = c + threadIdx.x; q < ld; q += blockDim.x) xo[q] = xp[q] * ip;
+        } else {
+            const double f = xs[c] * ip;
+            for (int q = c + threadIdx.x; q < ld; q += blockDim.x) xo[q] = fma(-f, xp[q], xs[q]);
+        }
+    }
+}
+
+__global__ void k_gj_store(const double *__restrict__ X, double *__restrict__ D, int nb)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(e / nb), c = (int)(e % nb);
+        D[e] = X[(size_t)r * 2 * nb + nb + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched FP64 GEMM on nb x nb row-major blocks: C = alpha A B + beta C.
+// ---------------------------------------------------------------------------
+constexpr int GB_MAX = 64;
+struct GemmBatch {
+    const double *A[GB_MAX];
+    const double *B[GB_MAX];
+    double *C[GB_MAX];
+};
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+__global__ void __launch_bounds__(256) k_dgemm(GemmBatch gb, int n, double alpha, double beta)
+{
+    __shared__ double As[TK][TM + 1];
+    __shared__ double Bs[TK][TN + 1];
+    const double *A = gb.A[blockIdx.z], *B = gb.B[blockIdx.z];
+    double *C = gb.C[blockIdx.z];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < n; k0 += TK) {
+        for (int e = threadIdx.x; e < TM * TK; e += 256) {
+            int r = e / TK, kk = e % TK;
+            int gr = row0 + r, gk = k0 + kk;
+            As[kk][r] = (gr < n && gk < n) ? A[(size_t)gr * n + gk] : 0.0;
+        }
+        for (int e = threadIdx.x; e < TK * TN; e += 256) {
+            int kk = e / TN, cc = e % TN;
+            int gk = k0 + kk, gc = col0 + cc;
+            Bs[kk][cc] = (gk < n && gc < n) ? B[(size_t)gk * n + gc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int gr = row0 + ty * 4 + i;
+        if (gr >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int gc = col0 + tx * 4 + j;
+            if (gc >= n) continue;
+            double *cp = C + (size_t)gr * n + gc;
+            *cp = beta == 0.0 ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *cp);
+        }
+    }
+}
+
+static int gemm_batch(bfs_ctx *c, std::vector<const double *> &A, std::vector<const double *> &B,
+                      std::vector<double *> &C, double alpha, double beta, cudaStream_t s)
+{
+    const int nb = c->nb;
+    for (size_t o = 0; o < A.size(); o += GB_MAX) {
+        GemmBatch gb;
+        int cnt = (int)std::min<size_t>(GB_MAX, A.size() - o);
+        for (int i = 0; i < cnt; i++) { gb.A[i] = A[o + i]; gb.B[i] = B[o + i]; gb.C[i] = C[o + i]; }
+        dim3 grid((nb + TN - 1) / TN, (nb + TM - 1) / TM, cnt);
+        k_dgemm<<<grid, 256, 0, s>>>(gb, nb, alpha, beta);
+        c->launches++;
+    }
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Apply: permutations between the order of u / F and the slice-interleaved order,
+// and one block-row GEMV per slice for each triangular sweep.
+// ---------------------------------------------------------------------------
+__global__ void k_perm_in(const double *__restrict__ r, double *__restrict__ x, int NB, int M)
+{
+    int n = 3 * NB * M;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
+        x[(size_t)l * 3 * NB + g * NB + p] = r[e];
+    }
+}
+
+__global__ void k_perm_out(const double *__restrict__ x, double *__restrict__ z, int NB, int M)
+{
+    int n = 3 * NB * M;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
+        z[e] = x[(size_t)l * 3 * NB + g * NB + p];
+    }
+}
+
+struct SweepArgs {
+    const double *blk[17];  // up to h + 1 blocks (h <= 16)
+    const double *vec[17];
+    double sgn[17];
+    int cnt;
+};
+
+// out[r] = (base ? base[r] : 0) + sum_b sgn_b (blk_b row r) . vec_b   (one warp per row)
+__global__ void k_sweep(SweepArgs sa, const double *__restrict__ base, double *__restrict__ out,
+                        int nb)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nb) return;
+    double acc = 0.0;
+    for (int b = 0; b < sa.cnt; b++) {
+        const double *row = sa.blk[b] + (size_t)warp * nb;
+        const double *v = sa.vec[b];
+        double t = 0.0;
+        for (int q = lane; q < nb; q += 32) t = fma(row[q], v[q], t);
+        acc = fma(sa.sgn[b], t, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[warp] = (base ? base[warp] : 0.0) + acc;
+}
+
+static PcArgs pc_args(const bfs_ctx *c, int h)
+{
+    PcArgs a;
+    a.N = c->N; a.M = c->M; a.half = c->half; a.h = h; a.nb = 3 * (c->N + 1);
+    a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy; a.F = c->F; a.n_rad = c->opt.n_rad;
+    a.xhi = c->x1 + (c->N - 1) * c->dx;
+    a.yhi = c->y1 + (c->M - 1) * c->dy;
+    a.ylo = c->half ? -a.yhi : c->y1;
+    return a;
+}
+
+void precond_free(bfs_ctx *c)
+{
+    cudaFree(c->d_pc);
+    cudaFree(c->d_gj);
+    cudaFree(c->d_rowsum5);
+    cudaFree(c->d_pivflag);
+    cudaFree(c->d_perm_a);
+    c->d_pc = c->d_gj = c->d_rowsum5 = c->d_perm_a = c->d_perm_b = nullptr;
+    c->d_pivflag = nullptr;
+    c->pc_ready = 0;
+}
+
+int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
+{
+    int h = half_band >= 0 ? half_band : c->opt.half_band;
+    if (h < 0) h = 0;
+    if (h > c->M - 1) h = c->M - 1;
+    if (h > 16) h = 16;  // the sweep kernel takes at most 17 blocks per row
+    precond_free(c);
+    const int nb = 3 * (c->N + 1), M = c->M, nd = 2 * h + 1;
+    c->nb = nb;
+    c->pc_h = h;
+    const size_t bsz = (size_t)nb * nb;
+    if (cudaMalloc(&c->d_pc, sizeof(double) * bsz * M * nd) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "preconditioner storage: out of device memory";
+        return BFS_ENOMEM;
+    }
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_gj, sizeof(double) * (bsz * 4 + bsz * (size_t)(h > 0 ? h : 1))));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_rowsum5, sizeof(double) * (size_t)c->Nt));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int)));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_perm_a, sizeof(double) * 2 * (size_t)c->n));
+    c->d_perm_b = c->d_perm_a + c->n;
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_pc, 0, sizeof(double) * bsz * M * nd, s));
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_pivflag, 0, sizeof(int), s));
+
+    PcArgs a = pc_args(c, h);
+    k_rowsum5<<<(c->Nt + 127) / 128, 128, 0, s>>>(a, c->d_rowsum5);
+    c->launches++;
+    k_form_dense<<<dim3(c->N - 1, nd, M), 128, sizeof(double) * (2 * c->N + 1), s>>>(a, c->d_pc,
+                                                                                  c->d_rowsum5);
+    c->launches++;
+    k_form_sparse<<<(M * nb + 127) / 128, 128, 0, s>>>(a, c->d_pc);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+
+    auto B = [&](int l, int m) { return c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz; };
+    double *X0 = c->d_gj, *X1 = c->d_gj + 2 * bsz, *tmp = c->d_gj + 4 * bsz;
+    const int gj_blocks = (nb + GJ_ROWS - 1) / GJ_ROWS;
+    for (int k = 0; k < M; k++) {
+        // D_k^-1 in place
+        k_gj_load<<<512, 256, 0, s>>>(B(k, k), X0, nb);
+        c->launches++;
+        double *xi = X0, *xo = X1;
+        for (int col = 0; col < nb; col++) {
+            k_gj_step<<<gj_blocks, 256, 0, s>>>(xi, xo, nb, col, c->d_pivflag);
+            c->launches++;
+            std::swap(xi, xo);
+        }
+        k_gj_store<<<512, 256, 0, s>>>(xi, B(k, k), nb);
+        c->launches++;
+        const int hi = std::min(M - 1, k + h);
+        if (hi > k) {
+            std::vector<const double *> A, Bm;
+            std::vector<double *> C;
+            // W_kj = D_k^-1 U_kj into tmp, then back into the U slots
+            for (int j = k + 1; j <= hi; j++) { A.push_back(B(k, k)); Bm.push_back(B(k, j)); C.push_back(tmp + (j - k - 1) * bsz); }
+            int rc = gemm_batch(c, A, Bm, C, 1.0, 0.0, s);
+            if (rc) return rc;
+            for (int j = k + 1; j <= hi; j++)
+                BFS_CUDA_TRY(c, cudaMemcpyAsync(B(k, j), tmp + (j - k - 1) * bsz, sizeof(double) * bsz,
+                                                cudaMemcpyDeviceToDevice, s));
+            // S_ij -= S_ik W_kj
+            A.clear(); Bm.clear(); C.clear();
+            for (int i = k + 1; i <= hi; i++)
+                for (int j = k + 1; j <= hi; j++) { A.push_back(B(i, k)); Bm.push_back(B(k, j)); C.push_back(B(i, j)); }
+            if ((rc = gemm_batch(c, A, Bm, C, -1.0, 1.0, s))) return rc;
+            // L_ik = S_ik D_k^-1
+            A.clear(); Bm.clear(); C.clear();
+            for (int i = k + 1; i <= hi; i++) { A.push_back(B(i, k)); Bm.push_back(B(k, k)); C.push_back(tmp + (i - k - 1) * bsz); }
+            if ((rc = gemm_batch(c, A, Bm, C, 1.0, 0.0, s))) return rc;
+            for (int i = k + 1; i <= hi; i++)
+                BFS_CUDA_TRY(c, cudaMemcpyAsync(B(i, k), tmp + (i - k - 1) * bsz, sizeof(double) * bsz,
+                                                cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    int flag = 0;
+    BFS_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_pivflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (flag) {
+        c->err = "zero pivot in a diagonal block of the preconditioner";
+        return BFS_ESINGULAR;
+    }
+    c->pc_ready = 1;
+    return BFS_OK;
+}
+
+int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
+{
+    if (!c->pc_ready) {
+        c->err = "preconditioner applied before bfs_precond_factor";
+        return BFS_ENOPREC;
+    }
+    const int nb = c->nb, M = c->M, h = c->pc_h, nd = 2 * h + 1, NB = c->N + 1;
+    const size_t bsz = (size_t)nb * nb;
+    double *x = c->d_perm_a, *y = c->d_perm_b;
+    const int g = (c->n + 255) / 256;
+    k_perm_in<<<g, 256, 0, s>>>(r, x, NB, M);
+    c->launches++;
+    auto B = [&](int l, int m) { return (const double *)(c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz); };
+    const int sweep_blocks = (nb * 32 + 255) / 256;
+    // forward: y_k = x_k - sum_{i<k} L_ki y_i  (in place in y)
+    for (int k = 0; k < M; k++) {
+        SweepArgs sa;
+        sa.cnt = 0;
+        for (int i = std::max(0, k - h); i < k; i++) {
+            sa.blk[sa.cnt] = B(k, i); sa.vec[sa.cnt] = y + (size_t)i * nb; sa.sgn[sa.cnt] = -1.0; sa.cnt++;
+        }
+        k_sweep<<<sweep_blocks, 256, 0, s>>>(sa, x + (size_t)k * nb, y + (size_t)k * nb, nb);
+        c->launches++;
+    }
+    // backward: x_k = D_k^-1 y_k - sum_{j>k} W_kj x_j  (result in x)
+    for (int k = M - 1; k >= 0; k--) {
+        SweepArgs sa;
+        sa.cnt = 0;
+        sa.blk[sa.cnt] = B(k, k); sa.vec[sa.cnt] = y + (size_t)k * nb; sa.sgn[sa.cnt] = 1.0; sa.cnt++;
+        for (int j = k + 1; j <= std::min(M - 1, k + h); j++) {
+            sa.blk[sa.cnt] = B(k, j); sa.vec[sa.cnt] = x + (size_t)j * nb; sa.sgn[sa.cnt] = -1.0; sa.cnt++;
+        }
+        k_sweep<<<sweep_blocks, 256, 0, s>>>(sa, nullptr, x + (size_t)k * nb, nb);
+        c->launches++;
+    }
+    k_perm_out<<<g, 256, 0, s>>>(x, z, NB, M);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+}  // namespace bfs

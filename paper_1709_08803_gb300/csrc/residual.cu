@@ -1,0 +1,522 @@
+// Nonlinear residual F(u) of the boundary-integral collocation scheme
+// (Buttle et al., arXiv:1709.08803, Sec. 2.2 and 3.1; ordering App. B).
+//
+// One residual is four launches on the caller's stream:
+//   k_unpack   trapezoid reconstruction of nodal zeta, phi, psi from u (Sec. 3.1)
+//   k_records  y-derivatives, source records (nodes and, in the half domain,
+//              their mirror images) and half-point target records
+//   k_pairs    the all-pairs quadrature: every half point of the free surface
+//              and of the bottom against every node of both sheets, with the
+//              (phi - phi*) / (psi - psi*) and S2 singularity subtractions
+//   k_finish   split reduction in FP64, closed-form I2'', the -2 pi (phi*-x*)
+//              term, the combined dynamic condition and the radiation rows
+#include <math.h>
+
+#include "bfs_internal.cuh"
+
+namespace bfs {
+
+// ---------------------------------------------------------------------------
+// Unpack: per slice j and field q, q(x1) followed by q_x at the N nodes; the
+// nodal values follow by the trapezoid rule along x (Sec. 3.1).
+// ---------------------------------------------------------------------------
+__global__ void k_unpack(const double *__restrict__ u, double *__restrict__ nodal, int N, int M,
+                         double dx)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * M) return;
+    int f = t / M, j = t - f * M;
+    size_t NM = (size_t)N * M;
+    const double *s = u + (size_t)f * (N + 1) * M + (size_t)j * (N + 1);
+    double *q = nodal + (size_t)(3 * f) * NM + (size_t)j * N;
+    double *qx = nodal + (size_t)(3 * f + 1) * NM + (size_t)j * N;
+    double prev = s[0], prevx = s[1];
+    q[0] = prev;
+    qx[0] = prevx;
+    for (int i = 1; i < N; i++) {
+        double cur = s[1 + i];
+        prev = prev + 0.5 * dx * (prevx + cur);
+        q[i] = prev;
+        qx[i] = cur;
+        prevx = cur;
+    }
+}
+
+// Second-order y-derivative at node (i, j); the half domain mirrors the
+// field across y = 0 (derivative 0 on that row).
+__device__ __forceinline__ double ydiff(const double *q, int N, int M, int half, double dy, int i,
+                                        int j)
+{
+    if (j == 0) {
+        if (half) return 0.0;
+        return (-3.0 * q[i] + 4.0 * q[i + N] - q[i + 2 * N]) / (2.0 * dy);
+    }
+    if (j == M - 1)
+        return (3.0 * q[i + (size_t)N * (M - 1)] - 4.0 * q[i + (size_t)N * (M - 2)] +
+                q[i + (size_t)N * (M - 3)]) / (2.0 * dy);
+    return (q[i + (size_t)N * (j + 1)] - q[i + (size_t)N * (j - 1)]) / (2.0 * dy);
+}
+
+struct RecArgs {
+    int N, M, half, Ns, Ns_cap, Nt;
+    double x1, y1, dx, dy, sigma, jc, ry;
+};
+
+// Builds source records [0, Ns_cap) and target records [0, Nt) in FP64 and FP32.
+__global__ void k_records(double *nodal, const double *__restrict__ beta,
+                          const double *__restrict__ bx, const double *__restrict__ by,
+                          double *__restrict__ src64, float *__restrict__ src32,
+                          double *__restrict__ tgt64, float *__restrict__ tgt32, RecArgs a)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = a.N, M = a.M;
+    const size_t NM = (size_t)N * M;
+    const double *z = nodal, *zx = nodal + NM, *ph = nodal + 3 * NM, *phx = nodal + 4 * NM;
+    const double *ps = nodal + 6 * NM;
+    double r[REC];
+    if (e < a.Ns_cap) {
+        if (e < a.Ns) {
+            int img = e >= (int)NM;
+            int i, j;
+            if (!img) { i = e % N; j = e / N; }
+            else { int q = e - (int)NM; i = q % N; j = 1 + q / N; }
+            size_t q = (size_t)j * N + i;
+            double zy = ydiff(z, N, M, a.half, a.dy, i, j);
+            if (!img) {  // the nodal y-derivatives are also an output (bfs_unpack)
+                nodal[2 * NM + q] = zy;
+                nodal[5 * NM + q] = ydiff(ph, N, M, a.half, a.dy, i, j);
+            }
+            double x = a.x1 + i * a.dx;
+            double cx = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+            double cy = a.half ? ((j == M - 1) ? 0.5 : 1.0) : ((j == 0 || j == M - 1) ? 0.5 : 1.0);
+            double w = a.dx * a.dy * cx * cy;
+            double w1 = w / (a.dx * a.dx), w2 = w / a.dx;
+            double ysg = img ? -1.0 : 1.0;
+            double f = ph[q] - x, g = ps[q] - x;
+            r[0] = (double)i - 0.5 * (N - 1);
+            r[1] = (ysg * j - a.jc) * a.ry;
+            r[2] = z[q] / a.dx;
+            r[3] = (beta[q] + 1.0) / a.dx;
+            r[4] = zx[q];
+            r[5] = ysg * zy;
+            r[6] = bx[q];
+            r[7] = ysg * by[q];
+            r[8] = w1 * f;
+            r[9] = w2 * zx[q];
+            r[10] = w1 * g;
+            r[11] = w2 * a.sigma * bx[q];
+            r[12] = w1;
+            r[13] = w2;
+            r[14] = 0.0;
+            r[15] = 0.0;
+        } else {  // padding: far away, zero weight
+            for (int k = 0; k < REC; k++) r[k] = 0.0;
+            r[0] = 1.0e6;
+        }
+        for (int k = 0; k < REC; k++) {
+            src64[(size_t)e * REC + k] = r[k];
+            src32[(size_t)e * REC + k] = (float)r[k];
+        }
+        return;
+    }
+    e -= a.Ns_cap;
+    if (e >= a.Nt) return;
+    int k = e % (N - 1), l = e / (N - 1);
+    size_t qa = (size_t)l * N + k, qb = qa + 1;
+    double xa = a.x1 + k * a.dx, xb = xa + a.dx;
+    double zs = 0.5 * (z[qa] + z[qb]);
+    double zxs = 0.5 * (zx[qa] + zx[qb]);
+    double zys = 0.5 * (ydiff(z, N, M, a.half, a.dy, k, l) + ydiff(z, N, M, a.half, a.dy, k + 1, l));
+    double pxs = 0.5 * (phx[qa] + phx[qb]);
+    double pys = 0.5 * (ydiff(ph, N, M, a.half, a.dy, k, l) + ydiff(ph, N, M, a.half, a.dy, k + 1, l));
+    double fs = 0.5 * ((ph[qa] - xa) + (ph[qb] - xb));
+    double gs = 0.5 * ((ps[qa] - xa) + (ps[qb] - xb));
+    double bs = 0.5 * (beta[qa] + beta[qb]);
+    r[0] = (double)k + 0.5 - 0.5 * (N - 1);
+    r[1] = ((double)l - a.jc) * a.ry;
+    r[2] = zs / a.dx;
+    r[3] = (bs + 1.0) / a.dx;
+    r[4] = zxs;
+    r[5] = zys;
+    r[6] = fs;
+    r[7] = gs;
+    r[8] = 1.0 + zxs * zxs;
+    r[9] = 2.0 * zxs * zys;
+    r[10] = 1.0 + zys * zys;
+    r[11] = zs / a.dx + 1.0 / a.dx;
+    r[12] = (bs + 1.0) / a.dx - 1.0 / a.dx;
+    r[13] = pxs;
+    r[14] = pys;
+    r[15] = 0.0;
+    for (int q = 0; q < TREC; q++) {
+        tgt64[(size_t)e * TREC + q] = r[q];
+        tgt32[(size_t)e * TREC + q] = (float)r[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// All-pairs quadrature.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <typename R> struct Vec;
+template <> struct Vec<float> { typedef float4 T; static constexpr int W = 4; };
+template <> struct Vec<double> { typedef double2 T; static constexpr int W = 2; };
+
+// Knuth's two-sum: hi + lo == a + b exactly.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
+{
+    float s = hi + b;
+    float bp = s - hi;
+    float err = (hi - (s - bp)) + (b - bp);
+    hi = s;
+    lo += err;
+}
+
+template <typename R, int TPB, int TPT, int CH, bool COMP>
+__global__ void __launch_bounds__(TPB)
+k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int Nt,
+        double *__restrict__ part)
+{
+    typedef typename Vec<R>::T V;
+    constexpr int VW = Vec<R>::W;
+    __shared__ __align__(16) R sh[CH * REC];
+    const int split = blockIdx.y;
+    const R *sb = src + (size_t)split * per_split * REC;
+
+    R tx[TPT], ty[TPT], tz[TPT], tB[TPT], tzx[TPT], tf[TPT], tg[TPT];
+    R cA[TPT], cB[TPT], cC[TPT], cTB[TPT], cBT[TPT];
+    int tid[TPT];
+#pragma unroll
+    for (int p = 0; p < TPT; p++) {
+        int t = blockIdx.x * TPB * TPT + p * TPB + threadIdx.x;
+        tid[p] = t;
+        const R *tr = tgt + (size_t)min(t, Nt - 1) * TREC;
+        tx[p] = tr[0]; ty[p] = tr[1]; tz[p] = tr[2]; tB[p] = tr[3]; tzx[p] = tr[4];
+        tf[p] = tr[6]; tg[p] = tr[7]; cA[p] = tr[8]; cB[p] = tr[9]; cC[p] = tr[10];
+        cTB[p] = tr[11]; cBT[p] = tr[12];
+    }
+    R hi[TPT][NACC], lo[TPT][NACC];
+#pragma unroll
+    for (int p = 0; p < TPT; p++)
+#pragma unroll
+        for (int q = 0; q < NACC; q++) { hi[p][q] = R(0); lo[p][q] = R(0); }
+
+    for (int c0 = 0; c0 < per_split; c0 += CH) {
+        __syncthreads();
+        const V *g = reinterpret_cast<const V *>(sb + (size_t)c0 * REC);
+        V *sv = reinterpret_cast<V *>(sh);
+        for (int e = threadIdx.x; e < CH * REC / VW; e += TPB) sv[e] = g[e];
+        __syncthreads();
+        R l[TPT][NACC];
+#pragma unroll
+        for (int p = 0; p < TPT; p++)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) l[p][q] = R(0);
+#pragma unroll 2
+        for (int s = 0; s < CH; s++) {
+            const R *r = sh + s * REC;
+            const R xs = r[0], ys = r[1], zs = r[2], bs = r[3];
+            const R zxs = r[4], zys = r[5], bxs = r[6], bys = r[7];
+            const R w1f = r[8], w2zx = r[9], w1g = r[10], w2sb = r[11];
+            const R w1 = r[12], w2 = r[13];
+#pragma unroll
+            for (int p = 0; p < TPT; p++) {
+                const R sx = xs - tx[p], sy = ys - ty[p];
+                const R syy = sy * sy;
+                const R rho2 = fma(sx, sx, syy);
+                // top target, top source: w (f - f*) K1 + w zeta_x K2, and w S2
+                {
+                    const R d = zs - tz[p];
+                    const R ri = rsq(fma(d, d, rho2));
+                    const R ri3 = ri * ri * ri;
+                    const R num = fma(-sy, zys, fma(-sx, zxs, d));
+                    const R dens = fma(-tf[p], w1, w1f);
+                    l[p][0] = fma(dens * num, ri3, l[p][0]);
+                    l[p][1] = fma(w2zx, ri, l[p][1]);
+                    const R qf = fma(sx, fma(cA[p], sx, cB[p] * sy), cC[p] * syy);
+                    l[p][2] = fma(w2, rsq(qf), l[p][2]);
+                }
+                // top target, bottom source: -w g K1(beta) + w sigma beta_x K2(beta)
+                {
+                    const R d = bs - cTB[p];
+                    const R ri = rsq(fma(d, d, rho2));
+                    const R ri3 = ri * ri * ri;
+                    const R num = fma(-sy, bys, fma(-sx, bxs, d));
+                    l[p][0] = fma(-(w1g * num), ri3, l[p][0]);
+                    l[p][1] = fma(w2sb, ri, l[p][1]);
+                }
+                // bottom target, top source: w f K1 + w zeta_x K2
+                {
+                    const R d = zs - cBT[p];
+                    const R ri = rsq(fma(d, d, rho2));
+                    const R ri3 = ri * ri * ri;
+                    const R num = fma(-sy, zys, fma(-sx, zxs, d));
+                    l[p][3] = fma(w1f * num, ri3, l[p][3]);
+                    l[p][4] = fma(w2zx, ri, l[p][4]);
+                }
+                // bottom target, bottom source: -w (g - g*) K1(beta)
+                {
+                    const R d = bs - tB[p];
+                    const R ri = rsq(fma(d, d, rho2));
+                    const R ri3 = ri * ri * ri;
+                    const R num = fma(-sy, bys, fma(-sx, bxs, d));
+                    const R dens = fma(-tg[p], w1, w1g);
+                    l[p][3] = fma(-(dens * num), ri3, l[p][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < TPT; p++)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) {
+                if constexpr (COMP) two_sum_acc(hi[p][q], lo[p][q], l[p][q]);
+                else hi[p][q] += l[p][q];
+            }
+    }
+#pragma unroll
+    for (int p = 0; p < TPT; p++) {
+        if (tid[p] >= Nt) continue;
+#pragma unroll
+        for (int q = 0; q < NACC; q++)
+            part[((size_t)split * NACC + q) * Nt + tid[p]] = (double)hi[p][q] + (double)lo[p][q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Closed-form integral of S2 = (A s^2 + B s t + C t^2)^(-1/2) over a rectangle
+// (Sec. 3.1).  The antiderivative printed in the paper is
+//   t/sqrt(A) ln(2As + Bt + 2 sqrt(A Q)) + s/sqrt(C) ln(2Ct + Bs + 2 sqrt(C Q));
+// where the log argument would cancel (2As + Bt < 0) it is evaluated as
+// ln((4AC - B^2) t^2) - ln(2 sqrt(AQ) - 2As - Bt), and t ln(.) -> 0 at t = 0.
+// ---------------------------------------------------------------------------
+__device__ double antideriv_S2(double A, double B, double C, double s, double t)
+{
+    const double Q = A * s * s + B * s * t + C * t * t;
+    const double D = 4.0 * A * C - B * B;
+    double g = 0.0;
+    if (t != 0.0) {
+        const double lin = 2.0 * A * s + B * t, r = 2.0 * sqrt(A * Q);
+        const double L = (lin >= 0.0) ? log(lin + r) : (log(D * t * t) - log(r - lin));
+        g += t * rsqrt(A) * L;
+    }
+    if (s != 0.0) {
+        const double lin = 2.0 * C * t + B * s, r = 2.0 * sqrt(C * Q);
+        const double L = (lin >= 0.0) ? log(lin + r) : (log(D * s * s) - log(r - lin));
+        g += s * rsqrt(C) * L;
+    }
+    return g;
+}
+
+__device__ double rect_S2(double A, double B, double C, double s1, double s2, double t1, double t2)
+{
+    return antideriv_S2(A, B, C, s2, t2) - antideriv_S2(A, B, C, s1, t2) -
+           antideriv_S2(A, B, C, s2, t1) + antideriv_S2(A, B, C, s1, t1);
+}
+
+struct FinArgs {
+    int N, M, Nt, splits;
+    double x1, y1, dx, dy, ylo, yhi, xhi, F, n_rad;
+};
+
+// F2 / F7 / F1 at every half point, radiation rows per slice.
+__global__ void k_finish(const double *__restrict__ part, const double *__restrict__ tgt,
+                         const double *__restrict__ constB, const double *__restrict__ nodal,
+                         double *__restrict__ Fu, int *__restrict__ flag, FinArgs a)
+{
+    const double TWO_PI = 6.283185307179586476925286766559;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = a.N, M = a.M;
+    const size_t blk = (size_t)(N + 1) * M;
+    bool bad = false;
+    if (e < a.Nt) {
+        int k = e % (N - 1), l = e / (N - 1);
+        double acc[NACC];
+#pragma unroll
+        for (int q = 0; q < NACC; q++) acc[q] = 0.0;
+        for (int s = 0; s < a.splits; s++)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) acc[q] += part[((size_t)s * NACC + q) * a.Nt + e];
+        const double *r = tgt + (size_t)e * TREC;
+        const double zs = r[2] * a.dx, zxs = r[4], zys = r[5], fs = r[6], gs = r[7];
+        const double A = r[8], B = r[9], C = r[10], pxs = r[13], pys = r[14];
+        const double xs = a.x1 + (k + 0.5) * a.dx, ys = a.y1 + l * a.dy;
+        const double I2pp = rect_S2(A, B, C, a.x1 - xs, a.xhi - xs, a.ylo - ys, a.yhi - ys);
+        const double F2 = acc[0] + acc[1] - zxs * acc[2] + zxs * I2pp - TWO_PI * fs;
+        const double F7 = acc[3] + acc[4] + constB[e] - TWO_PI * gs;
+        const double num = (1.0 + zxs * zxs) * pys * pys + (1.0 + zys * zys) * pxs * pxs -
+                           2.0 * zxs * zys * pxs * pys;
+        const double F1 = 0.5 * num / (1.0 + zxs * zxs + zys * zys) + zs / (a.F * a.F) - 0.5;
+        const size_t row = (size_t)l * (N + 1) + 2 + k;
+        Fu[row] = F1;
+        Fu[blk + row] = F2;
+        Fu[2 * blk + row] = F7;
+        bad = !isfinite(F1) || !isfinite(F2) || !isfinite(F7);
+    } else if (e < a.Nt + M) {
+        // radiation conditions of Scullen at x1 (Sec. 3.1); second derivatives
+        // are forward differences of the first derivatives
+        int l = e - a.Nt;
+        const size_t NM = (size_t)N * M, q = (size_t)l * N, row = (size_t)l * (N + 1);
+        const double x1 = a.x1, n = a.n_rad, h = a.dx;
+        for (int f = 0; f < 3; f++) {
+            const double v1 = nodal[(3 * f) * NM + q];
+            const double d1 = nodal[(3 * f + 1) * NM + q], d2 = nodal[(3 * f + 1) * NM + q + 1];
+            double Fa, Fb;
+            if (f == 0) {
+                Fa = x1 * d1 + n * v1;
+                Fb = x1 * (d2 - d1) / h + n * d1;
+            } else {
+                Fa = x1 * (d1 - 1.0) + n * (v1 - x1);
+                Fb = x1 * (d2 - d1) / h + n * (d1 - 1.0);
+            }
+            Fu[f * blk + row] = Fa;
+            Fu[f * blk + row + 1] = Fb;
+            bad = bad || !isfinite(Fa) || !isfinite(Fb);
+        }
+    }
+    if (bad) atomicOr(flag, 1);
+}
+
+// Bottom-only part of the bottom single layer seen from bottom half points:
+//   sigma [ sum w beta_x K2(beta; beta*) - beta_x* sum w S2_beta ] + sigma beta_x* I2''_beta
+// It depends on the topography alone, so it is evaluated once (FP64).
+__global__ void k_constB(const double *__restrict__ src, int Ns, const double *__restrict__ tgt,
+                         const double *__restrict__ bx, const double *__restrict__ by,
+                         double *__restrict__ out, FinArgs a, double sigma)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.Nt) return;
+    const int N = a.N;
+    int k = e % (N - 1), l = e / (N - 1);
+    size_t qa = (size_t)l * N + k, qb = qa + 1;
+    const double bxs = 0.5 * (bx[qa] + bx[qb]), bys = 0.5 * (by[qa] + by[qb]);
+    const double A = 1.0 + bxs * bxs, B = 2.0 * bxs * bys, C = 1.0 + bys * bys;
+    const double *t = tgt + (size_t)e * TREC;
+    const double tx = t[0], ty = t[1], tb = t[3];
+    double sK = 0.0, sS = 0.0;
+    for (int s = 0; s < Ns; s++) {
+        const double *r = src + (size_t)s * REC;
+        const double sx = r[0] - tx, sy = r[1] - ty, d = r[3] - tb;
+        sK += r[11] * rsqrt(sx * sx + sy * sy + d * d);
+        sS += r[13] * rsqrt(A * sx * sx + B * sx * sy + C * sy * sy);
+    }
+    const double xs = a.x1 + (k + 0.5) * a.dx, ys = a.y1 + l * a.dy;
+    const double I2pp = rect_S2(A, B, C, a.x1 - xs, a.xhi - xs, a.ylo - ys, a.yhi - ys);
+    out[e] = sK - sigma * bxs * sS + sigma * bxs * I2pp;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static RecArgs rec_args(const bfs_ctx *c)
+{
+    RecArgs a;
+    a.N = c->N; a.M = c->M; a.half = c->half; a.Ns = c->Ns; a.Ns_cap = c->Ns_cap; a.Nt = c->Nt;
+    a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy; a.sigma = c->opt.sign_I4;
+    a.jc = c->half ? 0.0 : 0.5 * (c->M - 1);
+    a.ry = c->dy / c->dx;
+    return a;
+}
+
+static FinArgs fin_args(const bfs_ctx *c, int splits)
+{
+    FinArgs a;
+    a.N = c->N; a.M = c->M; a.Nt = c->Nt; a.splits = splits;
+    a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy;
+    a.yhi = c->y1 + (c->M - 1) * c->dy;
+    a.ylo = c->half ? -a.yhi : c->y1;
+    a.xhi = c->x1 + (c->N - 1) * c->dx;
+    a.F = c->F; a.n_rad = c->opt.n_rad;
+    return a;
+}
+
+PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, int sms)
+{
+    PairPlan p;
+    p.tpb = tpb; p.tpt = tpt; p.chunk = chunk;
+    p.tiles = (Nt + tpb * tpt - 1) / (tpb * tpt);
+    int nchunks = (Ns + chunk - 1) / chunk;
+    int want = splits_req > 0 ? splits_req : (sms * 8 + p.tiles - 1) / p.tiles;
+    if (want < 1) want = 1;
+    if (want > nchunks) want = nchunks;
+    int cps = (nchunks + want - 1) / want;
+    p.splits = (nchunks + cps - 1) / cps;
+    p.per_split = cps * chunk;
+    return p;
+}
+
+int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s)
+{
+    k_unpack<<<(3 * c->M + 127) / 128, 128, 0, s>>>(u, c->d_nodal, c->N, c->M, c->dx);
+    c->launches++;
+    RecArgs ra = rec_args(c);
+    int tot = c->Ns_cap + c->Nt;
+    k_records<<<(tot + 255) / 256, 256, 0, s>>>(c->d_nodal, c->d_beta, c->d_bx, c->d_by, c->d_src64,
+                                                 c->d_src32, c->d_tgt64, c->d_tgt32, ra);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// Launch configurations of the pair kernels.
+constexpr int P64_TPB = 128, P64_TPT = 1, P64_CH = 32;
+constexpr int P32_TPB = 128, P32_TPT = 2, P32_CH = 128;
+
+int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cudaStream_t s)
+{
+    int rc = unpack_launch(c, u, s);
+    if (rc) return rc;
+    const PairPlan &p = precision == BFS_FP32C ? c->plan32 : c->plan64;
+    dim3 grid(p.tiles, p.splits);
+    cudaEvent_t ev1 = nullptr;
+    if (c->prof_on) {
+        cudaEvent_t ev0 = prof_event(c);
+        ev1 = prof_event(c);
+        c->ev_kind.push_back(precision == BFS_FP32C ? 1 : 0);
+        cudaEventRecord(ev0, s);
+    }
+    if (precision == BFS_FP32C)
+        k_pairs<float, P32_TPB, P32_TPT, P32_CH, true>
+            <<<grid, P32_TPB, 0, s>>>(c->d_src32, p.per_split, c->d_tgt32, c->Nt, c->d_part);
+    else
+        k_pairs<double, P64_TPB, P64_TPT, P64_CH, false>
+            <<<grid, P64_TPB, 0, s>>>(c->d_src64, p.per_split, c->d_tgt64, c->Nt, c->d_part);
+    c->launches++;
+    if (ev1) cudaEventRecord(ev1, s);
+    FinArgs fa = fin_args(c, p.splits);
+    int tot = c->Nt + c->M;
+    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, Fu,
+                                               c->d_flag, fa);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+int constB_launch(bfs_ctx *c, cudaStream_t s)
+{
+    FinArgs fa = fin_args(c, 1);
+    k_constB<<<(c->Nt + 127) / 128, 128, 0, s>>>(c->d_src64, c->Ns, c->d_tgt64, c->d_bx, c->d_by,
+                                                 c->d_constB, fa, c->opt.sign_I4);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+cudaEvent_t prof_event(bfs_ctx *c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+void plans_for(int Nt, int Ns, int splits_req, int sms, PairPlan *p64, PairPlan *p32)
+{
+    *p64 = make_plan(Nt, Ns, P64_TPB, P64_TPT, P64_CH, splits_req, sms);
+    *p32 = make_plan(Nt, Ns, P32_TPB, P32_TPT, P32_CH, splits_req, sms);
+}
+
+}  // namespace bfs

@@ -1,0 +1,431 @@
+// Jacobian-free Newton-Krylov driver (Buttle et al., arXiv:1709.08803, Sec. 3.2):
+// damped Newton u <- u + mu du with a backtracking line search, du from
+// right-preconditioned restarted GMRES (Saad & Schultz) on J P^-1, and
+// J P^-1 v approximated by the forward difference (F(u + h P^-1 v) - F(u)) / h.
+//
+// Every vector operation runs on the device in FP64: Arnoldi with classical
+// Gram-Schmidt applied twice, Givens rotations, the triangular solve and the
+// update.  The host only reads one scalar per Arnoldi step (the GMRES residual
+// estimate) and one per line-search trial.
+#include <math.h>
+#include <chrono>
+
+#include "bfs_internal.cuh"
+
+namespace bfs {
+
+constexpr int RED_BLOCKS = 256;
+constexpr int RED_TPB = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// partial[j * RED_BLOCKS + b] = sum over block b's slice of V_j . w   (grid: RED_BLOCKS x cnt)
+__global__ void k_dots(const double *__restrict__ V, size_t ldv, const double *__restrict__ w,
+                       int n, double *__restrict__ partial)
+{
+    __shared__ double sh[RED_TPB / 32];
+    const int j = blockIdx.y;
+    const double *v = V + (size_t)j * ldv;
+    double acc = 0.0;
+    for (int i = blockIdx.x * RED_TPB + threadIdx.x; i < n; i += RED_BLOCKS * RED_TPB)
+        acc = fma(v[i], w[i], acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < RED_TPB / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) partial[(size_t)j * RED_BLOCKS + blockIdx.x] = t;
+    }
+}
+
+// out[j] = sum_b partial[j * RED_BLOCKS + b]   (one block per j, fixed order)
+__global__ void k_dots_final(const double *__restrict__ partial, double *__restrict__ out)
+{
+    __shared__ double sh[RED_BLOCKS / 32];
+    const int j = blockIdx.x;
+    double t = partial[(size_t)j * RED_BLOCKS + threadIdx.x];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double q = threadIdx.x < RED_BLOCKS / 32 ? sh[threadIdx.x] : 0.0;
+        q = warp_sum(q);
+        if (threadIdx.x == 0) out[j] = q;
+    }
+}
+
+// out2 = |v|_2^2 partials (slot 0) and |v|_inf partials (slot 1)
+__global__ void k_norms(const double *__restrict__ v, int n, double *__restrict__ partial)
+{
+    __shared__ double s2[RED_TPB / 32], si[RED_TPB / 32];
+    double a = 0.0, m = 0.0;
+    for (int i = blockIdx.x * RED_TPB + threadIdx.x; i < n; i += RED_BLOCKS * RED_TPB) {
+        double x = v[i];
+        a = fma(x, x, a);
+        m = fmax(m, fabs(x));
+        if (x != x) m = x;  // propagate NaN
+    }
+    a = warp_sum(a);
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) { s2[threadIdx.x >> 5] = a; si[threadIdx.x >> 5] = m; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double p = threadIdx.x < RED_TPB / 32 ? s2[threadIdx.x] : 0.0;
+        double q = threadIdx.x < RED_TPB / 32 ? si[threadIdx.x] : 0.0;
+        p = warp_sum(p);
+        q = warp_max(q);
+        if (threadIdx.x == 0) { partial[blockIdx.x] = p; partial[RED_BLOCKS + blockIdx.x] = q; }
+    }
+}
+
+__global__ void k_norms_final(const double *__restrict__ partial, double *out2, double *outinf)
+{
+    __shared__ double s2[RED_BLOCKS / 32], si[RED_BLOCKS / 32];
+    double p = partial[threadIdx.x], q = partial[RED_BLOCKS + threadIdx.x];
+    p = warp_sum(p);
+    q = warp_max(q);
+    if ((threadIdx.x & 31) == 0) { s2[threadIdx.x >> 5] = p; si[threadIdx.x >> 5] = q; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        p = threadIdx.x < RED_BLOCKS / 32 ? s2[threadIdx.x] : 0.0;
+        q = threadIdx.x < RED_BLOCKS / 32 ? si[threadIdx.x] : 0.0;
+        p = warp_sum(p);
+        q = warp_max(q);
+        if (threadIdx.x == 0) {
+            if (out2) *out2 = sqrt(p);
+            if (outinf) *outinf = q;
+        }
+    }
+}
+
+void norms_launch(bfs_ctx *c, const double *v, int n, double *d_out2, double *d_outinf,
+                  cudaStream_t s)
+{
+    k_norms<<<RED_BLOCKS, RED_TPB, 0, s>>>(v, n, c->d_red);
+    c->launches++;
+    k_norms_final<<<1, RED_BLOCKS, 0, s>>>(c->d_red, d_out2, d_outinf);
+    c->launches++;
+}
+
+// y = a x + b z, with a and/or b read from device scalars when the pointer is given
+__global__ void k_axpby(double *y, const double *x,
+                        const double *z, int n, double a, double b,
+                        const double *__restrict__ dscale_b)
+{
+    double bb = dscale_b ? b * *dscale_b : b;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = a * x[i] + bb * z[i];
+}
+
+// h = h_rel (1 + |u|) / |z| into sc[4]; 1/h into sc[5]; sc[6] = 1 when z == 0.
+__global__ void k_jv_step(double *sc, double h_fixed, double h_rel)
+{
+    double nu = sc[0], nz = sc[1];
+    double h = h_fixed > 0.0 ? h_fixed : (nz > 0.0 ? h_rel * (1.0 + nu) / nz : 0.0);
+    sc[4] = h;
+    sc[5] = h > 0.0 ? 1.0 / h : 0.0;
+    sc[6] = (nz > 0.0) ? 0.0 : 1.0;
+}
+
+// Jz = (Fp - Fu) / h
+__global__ void k_jv_diff(double *__restrict__ Jz, const double *__restrict__ Fp,
+                          const double *__restrict__ Fu, int n, const double *__restrict__ sc)
+{
+    double ih = sc[5];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        Jz[i] = (Fp[i] - Fu[i]) * ih;
+}
+
+static int grid_for(int n) { return (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184; }
+
+int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
+               double h, int precision, cudaStream_t s)
+{
+    const int n = c->n;
+    double h_rel = c->opt.jv_h_rel;
+    if (!(h_rel > 0.0)) h_rel = precision == BFS_FP32C ? 3.4526698e-4 : 1.4901161193847656e-8;
+    if (!(h > 0.0)) {
+        norms_launch(c, u, n, c->d_scal + 0, nullptr, s);
+        norms_launch(c, z, n, c->d_scal + 1, nullptr, s);
+    }
+    k_jv_step<<<1, 1, 0, s>>>(c->d_scal, h, h_rel);
+    c->launches++;
+    // u + h z (a zero z gives h = 0 and Jz = 0)
+    k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_up, u, z, n, 1.0, 1.0, c->d_scal + 4);
+    c->launches++;
+    int rc = residual_launch(c, c->d_up, c->d_Fp, precision, s);
+    if (rc) return rc;
+    k_jv_diff<<<grid_for(n), 256, 0, s>>>(Jz, c->d_Fp, Fu, n, c->d_scal);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// w -= V[0..cnt) h   (h on the device)
+__global__ void k_gemv_sub(double *__restrict__ w, const double *__restrict__ V, size_t ldv,
+                           const double *__restrict__ h, int cnt, int n)
+{
+    __shared__ double hs[128];
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = w[i];
+        for (int j = 0; j < cnt; j++) acc = fma(-hs[j], V[(size_t)j * ldv + i], acc);
+        w[i] = acc;
+    }
+}
+
+// x = V[0..cnt) y
+__global__ void k_gemv(double *__restrict__ x, const double *__restrict__ V, size_t ldv,
+                       const double *__restrict__ y, int cnt, int n)
+{
+    __shared__ double ys[128];
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < cnt; j++) acc = fma(ys[j], V[(size_t)j * ldv + i], acc);
+        x[i] = acc;
+    }
+}
+
+// V_{j+1} = w / |w| (|w| at *nrm; a zero norm leaves zeros)
+__global__ void k_scale_into(double *__restrict__ out, const double *__restrict__ w, int n,
+                             const double *__restrict__ nrm)
+{
+    double s = *nrm > 0.0 ? 1.0 / *nrm : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = w[i] * s;
+}
+
+// Givens step for column j: H(0..j, j) = h + h2, H(j+1, j) = |w|; rotate with
+// the stored rotations, form the new one, update g; residual estimate |g_{j+1}|
+// goes to res.  Layout of giv: cs[m] sn[m] g[m+1] y[m] h[m+1] h2[m+1].
+__global__ void k_givens(double *H, double *giv, int m, int j, const double *hn, double *res)
+{
+    double *cs = giv, *sn = giv + m, *g = giv + 2 * m, *h = giv + 4 * m + 1,
+           *h2 = giv + 5 * m + 2;
+    double *col = H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; i++) col[i] = h[i] + h2[i];
+    col[j + 1] = *hn;
+    for (int i = 0; i < j; i++) {
+        double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    double a = col[j], b = col[j + 1];
+    double d = hypot(a, b);
+    cs[j] = d > 0.0 ? a / d : 1.0;
+    sn[j] = d > 0.0 ? b / d : 0.0;
+    col[j] = d;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    *res = fabs(g[j + 1]);
+}
+
+// g = (beta, 0, ..., 0) and V_0 scale factor
+__global__ void k_gmres_init(double *giv, int m, const double *beta)
+{
+    double *g = giv + 2 * m;
+    for (int i = 0; i <= m; i++) g[i] = 0.0;
+    g[0] = *beta;
+}
+
+// Back substitution H(0..k,0..k) y = g(0..k) into y
+__global__ void k_trisolve(const double *H, double *giv, int m, int k)
+{
+    double *g = giv + 2 * m, *y = giv + 3 * m + 1;
+    for (int i = k - 1; i >= 0; i--) {
+        double s = g[i];
+        for (int q = i + 1; q < k; q++) s -= H[(size_t)q * (m + 1) + i] * y[q];
+        y[i] = s / H[(size_t)i * (m + 1) + i];
+    }
+}
+
+int alloc_solver(bfs_ctx *c)
+{
+    if (c->d_V) return BFS_OK;
+    const int m = c->opt.gmres_restart, n = c->n;
+    c->m_alloc = m;
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_V, sizeof(double) * (size_t)(m + 1) * n));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_H, sizeof(double) * (size_t)(m + 1) * m));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_giv, sizeof(double) * (size_t)(6 * m + 4)));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_sbase, sizeof(double) * (size_t)8 * n));
+    double *b = c->d_sbase;
+    c->d_F = b; c->d_du = b + n; c->d_ut = b + 2 * (size_t)n; c->d_Ft = b + 3 * (size_t)n;
+    c->d_z = b + 4 * (size_t)n; c->d_w = b + 5 * (size_t)n; c->d_F32 = b + 6 * (size_t)n;
+    c->d_uio = b + 7 * (size_t)n;
+    BFS_CUDA_TRY(c, cudaMallocHost(&c->h_pin, sizeof(double) * 16));
+    return BFS_OK;
+}
+
+static int read_scalars(bfs_ctx *c, const double *d, int cnt, cudaStream_t s)
+{
+    BFS_CUDA_TRY(c, cudaMemcpyAsync(c->h_pin, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+// CGS2 orthogonalisation of w against V[0..cnt); h + h2 in giv; |w| in d_scal[8]
+static void arnoldi_orth(bfs_ctx *c, int cnt, cudaStream_t s)
+{
+    const int m = c->m_alloc, n = c->n;
+    double *h = c->d_giv + 4 * m + 1, *h2 = c->d_giv + 5 * m + 2;
+    const size_t ldv = (size_t)n;
+    for (int pass = 0; pass < 2; pass++) {
+        double *hp = pass ? h2 : h;
+        k_dots<<<dim3(RED_BLOCKS, cnt), RED_TPB, 0, s>>>(c->d_V, ldv, c->d_w, n, c->d_red);
+        c->launches++;
+        k_dots_final<<<cnt, RED_BLOCKS, 0, s>>>(c->d_red, hp);
+        c->launches++;
+        k_gemv_sub<<<grid_for(n), 256, 0, s>>>(c->d_w, c->d_V, ldv, hp, cnt, n);
+        c->launches++;
+    }
+    norms_launch(c, c->d_w, n, c->d_scal + 8, nullptr, s);
+}
+
+// GMRES for J P^-1 y = -F at u; du = P^-1 V y.  Returns status; *its gets iterations.
+static int gmres(bfs_ctx *c, const double *u, const double *F, const double *Fbase, double fnorm2,
+                 double eta, int maxit, int *its_out, int *precs, int *jvs, cudaStream_t s)
+{
+    const int m = c->m_alloc, n = c->n;
+    const size_t ldv = (size_t)n;
+    int its = 0, rc;
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_du, 0, sizeof(double) * n, s));
+    // r = -F
+    k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, F, n, -1.0, 0.0, nullptr);
+    c->launches++;
+    const double target = eta * fnorm2;
+    int status = BFS_OK;
+    while (true) {
+        norms_launch(c, c->d_w, n, c->d_scal + 8, nullptr, s);
+        if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
+        double beta = c->h_pin[0];
+        if (!isfinite(beta)) return BFS_ENAN;
+        if (beta <= target || its >= maxit) break;
+        k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V, c->d_w, n, c->d_scal + 8);
+        c->launches++;
+        k_gmres_init<<<1, 1, 0, s>>>(c->d_giv, m, c->d_scal + 8);
+        c->launches++;
+        int j = 0;
+        double res = beta;
+        for (; j < m && its < maxit; j++) {
+            double *vj = c->d_V + (size_t)j * ldv;
+            if ((rc = precond_apply(c, vj, c->d_z, s))) return rc;
+            (*precs)++;
+            if ((rc = jvp_launch(c, u, Fbase, c->d_z, c->d_w, 0.0, c->opt.krylov_precision, s))) return rc;
+            (*jvs)++;
+            arnoldi_orth(c, j + 1, s);
+            k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V + (size_t)(j + 1) * ldv, c->d_w, n,
+                                                     c->d_scal + 8);
+            c->launches++;
+            k_givens<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, j, c->d_scal + 8, c->d_scal + 9);
+            c->launches++;
+            if ((rc = read_scalars(c, c->d_scal + 8, 2, s))) return rc;
+            its++;
+            res = c->h_pin[1];
+            if (!isfinite(res)) return BFS_ENAN;
+            if (res <= target) { j++; break; }
+            if (c->h_pin[0] == 0.0) { j++; break; }  // invariant subspace reached
+        }
+        // du += P^-1 V y
+        k_trisolve<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, j);
+        c->launches++;
+        k_gemv<<<grid_for(n), 256, 0, s>>>(c->d_w, c->d_V, ldv, c->d_giv + 3 * m + 1, j, n);
+        c->launches++;
+        if ((rc = precond_apply(c, c->d_w, c->d_z, s))) return rc;
+        (*precs)++;
+        k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_du, c->d_du, c->d_z, n, 1.0, 1.0, nullptr);
+        c->launches++;
+        if (res <= target || its >= maxit) break;
+        // restart: r = -F - J du
+        if ((rc = jvp_launch(c, u, Fbase, c->d_du, c->d_w, 0.0, c->opt.krylov_precision, s))) return rc;
+        (*jvs)++;
+        k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, c->d_w, n, -1.0, -1.0, nullptr);
+        c->launches++;
+    }
+    *its_out = its;
+    return status;
+}
+
+int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
+{
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    const int n = c->n;
+    int rc = alloc_solver(c);
+    if (rc) return rc;
+    if (!c->pc_ready && (rc = precond_factor(c, c->opt.half_band, s))) return rc;
+    bfs_stats S{};
+    int precs = 0, jvs = 0;
+    auto finish = [&](int status) {
+        S.status = status;
+        S.seconds = std::chrono::duration<double>(clk::now() - t0).count();
+        S.precond_applies = precs;
+        if (c->opt.krylov_precision == BFS_FP32C) S.residual_evals_fp32 += jvs;
+        else S.residual_evals_fp64 += jvs;
+        if (st) *st = S;
+        return status;
+    };
+    if ((rc = residual_launch(c, u, c->d_F, BFS_FP64, s))) return finish(rc);
+    S.residual_evals_fp64++;
+    norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
+    if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
+    double f2 = c->h_pin[0], finf = c->h_pin[1];
+    for (int k = 0;; k++) {
+        S.fnorm_2 = f2;
+        S.fnorm_inf = finf;
+        if (!isfinite(f2) || !isfinite(finf)) return finish(BFS_ENAN);
+        if (finf <= c->opt.tol) return finish(BFS_OK);
+        if (k >= c->opt.max_newton) return finish(BFS_ENOCONV);
+        if (c->opt.time_budget_s > 0.0 &&
+            std::chrono::duration<double>(clk::now() - t0).count() > c->opt.time_budget_s)
+            return finish(BFS_ETIMEOUT);
+        int its = 0;
+        // the finite difference must subtract a residual of the same arithmetic
+        const double *Fbase = c->d_F;
+        if (c->opt.krylov_precision == BFS_FP32C) {
+            if ((rc = residual_launch(c, u, c->d_F32, BFS_FP32C, s))) return finish(rc);
+            S.residual_evals_fp32++;
+            Fbase = c->d_F32;
+        }
+        rc = gmres(c, u, c->d_F, Fbase, f2, c->opt.eta, c->opt.max_krylov, &its, &precs, &jvs, s);
+        S.krylov_its += its;
+        if (rc) return finish(rc);
+        double mu = 1.0;
+        bool ok = false;
+        while (mu >= 1e-4) {
+            k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_ut, u, c->d_du, n, 1.0, mu, nullptr);
+            c->launches++;
+            if ((rc = residual_launch(c, c->d_ut, c->d_Ft, BFS_FP64, s))) return finish(rc);
+            S.residual_evals_fp64++;
+            norms_launch(c, c->d_Ft, n, c->d_scal + 12, c->d_scal + 13, s);
+            if ((rc = read_scalars(c, c->d_scal + 12, 2, s))) return finish(rc);
+            if (isfinite(c->h_pin[0]) && c->h_pin[0] <= (1.0 - 1e-4 * mu) * f2) {
+                ok = true;
+                break;
+            }
+            mu *= 0.5;
+        }
+        if (!ok) return finish(BFS_ELINESEARCH);
+        f2 = c->h_pin[0];
+        finf = c->h_pin[1];
+        BFS_CUDA_TRY(c, cudaMemcpyAsync(u, c->d_ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        std::swap(c->d_F, c->d_Ft);
+        S.newton_its = k + 1;
+    }
+}
+
+}  // namespace bfs

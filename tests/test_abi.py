@@ -1,0 +1,95 @@
+"""The C ABI without a GPU: the library builds and loads, exports every entry
+point include/bfs.h declares, and rejects invalid problems on the host before
+any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1709_08803_gb300 import build as B
+from paper_1709_08803_gb300 import bfs
+from paper_1709_08803_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bfs.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return bfs.lib()
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bfs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("bfs_setup", "bfs_residual", "bfs_jvp", "bfs_precond_factor", "bfs_precond_apply",
+                 "bfs_solve", "bfs_destroy", "bfs_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [n for n in declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_default_options(L):
+    o = bfs.default_options()
+    assert o.n_rad == 0.05 and o.sign_I4 == -1.0 and o.tol == 1e-8
+    assert o.gmres_restart == 50 and o.krylov_precision == bfs.BFS_FP64
+
+
+def _setup(mesh, topo, F, opts=None):
+    m = bfs.bfs_mesh(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (topo.beta, topo.beta_x, topo.beta_y)]
+    D = ctypes.POINTER(ctypes.c_double)
+    t = bfs.bfs_topo(*[a.ctypes.data_as(D) for a in arrs])
+    o = opts if opts is not None else bfs.default_options()
+    ctx = ctypes.c_void_p()
+    rc = bfs.lib().bfs_setup(ctypes.byref(m), ctypes.byref(t), F, ctypes.byref(o), ctypes.byref(ctx))
+    return rc, ctx
+
+
+@pytest.mark.parametrize("case", ["N", "M", "dx", "F", "half_y1", "beta_pierces", "nan", "restart", "sign"])
+def test_setup_rejects_invalid_input(L, case):
+    mesh = W.mesh_box(9, 5, 0.4, 0.4)
+    topo = W.gaussian_bumps(mesh, [(0.1, 0.7, 0.0, 0.0)])
+    F, opts = 0.7, None
+    if case == "N":
+        mesh = W.Mesh(N=3, M=5, x1=-1, y1=-1, dx=0.4, dy=0.4)
+        topo = W.flat_topography(mesh)
+    elif case == "M":
+        mesh = W.Mesh(N=9, M=2, x1=-1, y1=-1, dx=0.4, dy=0.4)
+        topo = W.flat_topography(mesh)
+    elif case == "dx":
+        mesh = W.Mesh(N=9, M=5, x1=-1, y1=-1, dx=0.0, dy=0.4)
+    elif case == "F":
+        F = -0.5
+    elif case == "half_y1":
+        mesh = W.Mesh(N=9, M=5, x1=-1, y1=-0.4, dx=0.4, dy=0.4, half=1)
+    elif case == "beta_pierces":
+        topo = W.gaussian_bumps(mesh, [(1.2, 0.7, 0.0, 0.0)])
+    elif case == "nan":
+        b = topo.beta.copy()
+        b[3] = np.nan
+        topo = W.Topography(b, topo.beta_x, topo.beta_y)
+    elif case == "restart":
+        opts = bfs.default_options(gmres_restart=0)
+    elif case == "sign":
+        opts = bfs.default_options(sign_I4=0.5)
+    rc, ctx = _setup(mesh, topo, F, opts)
+    assert rc == bfs.BFS_EINVAL and not ctx.value
+    assert bfs.lib().bfs_last_error(None)
+
+
+def test_null_arguments_are_rejected(L):
+    assert L.bfs_residual(None, None, None, 0, None) == bfs.BFS_EINVAL
+    assert L.bfs_solve(None, None, None, None) == bfs.BFS_EINVAL
+    assert L.bfs_precond_apply(None, None, None, None) == bfs.BFS_EINVAL
+    L.bfs_destroy(None)

@@ -1,0 +1,247 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+Tolerances (written here, derived in the design notes):
+  FP64 residual: |F_gpu - F_oracle| <= 1e-10 * scale_row + 1e-13 per row, where
+      scale_row is the sum of |terms| of that row (so the bar stays meaningful
+      where F ~ 0).
+  FP32C residual: the measured error is reported; the test bar is 2e-6 * scale.
+  Nodal reconstruction: 1e-12 absolute (same trapezoid recurrence).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1709_08803_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_08803_gb300 import build
+    build.build()
+
+
+def _ctx(mesh, topo, F, **kw):
+    from paper_1709_08803_gb300 import bfs
+    return bfs.Context(mesh, topo, F, bfs.default_options(**kw))
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+MESHES = {
+    "small_half_31x11": (W.config_small_half()[0], 0.7),
+    "ragged_full_23x9": (W.Mesh(N=23, M=9, x1=-3.3, y1=-1.4, dx=0.3, dy=0.35), 0.8),
+    "full_61x21": (W.mesh_box(61, 21, 0.3, 0.3), 0.7),
+    "half_45x13": (W.Mesh(N=45, M=13, x1=-4.4, y1=0.0, dx=0.4, dy=0.4, half=1), 1.3),
+    "minimum_4x3": (W.Mesh(N=4, M=3, x1=-0.6, y1=-0.3, dx=0.3, dy=0.3), 0.9),
+}
+
+
+def _topo(mesh):
+    if mesh.N < 8:
+        return W.gaussian_bumps(mesh, [(0.05, 0.5, 0.0, 0.0)])
+    bumps = [(0.15, 0.8, 0.2, 0.0)] if mesh.half else [(0.15, 0.8, 0.2, 0.3), (0.08, 0.6, -0.5, -0.4)]
+    return W.gaussian_bumps(mesh, bumps)
+
+
+def _guesses(mesh):
+    return {"flat": W.flat_guess(mesh), "smooth": W.smooth_guess(mesh, 1),
+            "perturbed": W.perturbed_guess(mesh, 2, 1e-2)}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_residual_fp64_matches_oracle(name):
+    from paper_1709_08803_gb300 import bfs
+    mesh, F = MESHES[name]
+    topo = _topo(mesh)
+    ctx = _ctx(mesh, topo, F)
+    P = O.problem(mesh, F)
+    for gname, u in _guesses(mesh).items():
+        ref, sc = O.residual(P, topo, u, with_scale=True)
+        got = ctx.residual(_dev(u), precision=bfs.BFS_FP64).cpu().numpy()
+        err = np.abs(got - ref)
+        assert np.all(err <= TOL64 * sc + 1e-13), (name, gname, float((err / (sc + 1e-300)).max()))
+        assert ctx.check_finite()
+
+
+@pytest.mark.parametrize("name", ["small_half_31x11", "full_61x21", "half_45x13"])
+def test_residual_fp32c_error_bound(name):
+    from paper_1709_08803_gb300 import bfs
+    mesh, F = MESHES[name]
+    topo = _topo(mesh)
+    ctx = _ctx(mesh, topo, F)
+    P = O.problem(mesh, F)
+    for gname, u in _guesses(mesh).items():
+        ref, sc = O.residual(P, topo, u, with_scale=True)
+        got = ctx.residual(_dev(u), precision=bfs.BFS_FP32C).cpu().numpy()
+        rel = np.abs(got - ref) / (sc + 1e-300)
+        print(f"FP32C {name} {gname}: max |dF|/scale = {rel.max():.3e}")
+        assert rel.max() <= TOL32, (name, gname, rel.max())
+
+
+@pytest.mark.parametrize("name", ["small_half_31x11", "ragged_full_23x9"])
+def test_unpack_matches_oracle(name):
+    mesh, F = MESHES[name]
+    ctx = _ctx(mesh, _topo(mesh), F)
+    u = W.smooth_guess(mesh, 4)
+    ref = O.nodal_values(O.problem(mesh, F), u)
+    got = ctx.unpack(_dev(u))
+    for k, v in ref.items():
+        assert np.abs(got[k].cpu().numpy() - v).max() < 1e-12, k
+
+
+def test_jvp_matches_oracle_difference_quotient():
+    from paper_1709_08803_gb300 import bfs
+    mesh, F = MESHES["ragged_full_23x9"]
+    topo = _topo(mesh)
+    ctx = _ctx(mesh, topo, F)
+    P = O.problem(mesh, F)
+    u = W.smooth_guess(mesh, 5)
+    z = np.random.default_rng(9).standard_normal(mesh.n_unknowns)
+    h = 1e-5
+    ref = (O.residual(P, topo, u + h * z) - O.residual(P, topo, u)) / h
+    Fu = ctx.residual(_dev(u))
+    got = ctx.jvp(_dev(u), Fu, _dev(z), h=h, precision=bfs.BFS_FP64).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
+    # z = 0 gives exactly zero
+    zero = ctx.jvp(_dev(u), Fu, torch.zeros_like(Fu)).cpu().numpy()
+    assert not zero.any()
+
+
+@pytest.mark.parametrize("half_band", [0, 1, 3])
+@pytest.mark.parametrize("name", ["ragged_full_23x9", "small_half_31x11"])
+def test_precond_apply_matches_dense_solve(name, half_band):
+    mesh, F = MESHES[name]
+    ctx = _ctx(mesh, _topo(mesh), F)
+    ctx.precond_factor(half_band)
+    Jb = O.jtilde(O.problem(mesh, F), half_band=half_band)
+    r = np.random.default_rng(11).standard_normal(mesh.n_unknowns)
+    ref = np.linalg.solve(Jb, r)
+    got = ctx.precond_apply(_dev(r)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    # P z = r holds to rounding
+    assert np.abs(Jb @ got - r).max() <= 1e-9 * np.abs(r).max() * np.abs(Jb).max()
+
+
+def test_precond_apply_before_factor_is_an_error():
+    from paper_1709_08803_gb300 import bfs
+    mesh, F = MESHES["minimum_4x3"]
+    ctx = _ctx(mesh, _topo(mesh), F)
+    with pytest.raises(bfs.BfsError) as e:
+        ctx.precond_apply(_dev(np.ones(mesh.n_unknowns)))
+    assert e.value.code == bfs.BFS_ENOPREC
+
+
+def test_nan_input_is_flagged():
+    from paper_1709_08803_gb300 import bfs
+    mesh, F = MESHES["ragged_full_23x9"]
+    ctx = _ctx(mesh, _topo(mesh), F)
+    u = W.flat_guess(mesh)
+    u[17] = np.nan
+    ctx.residual(_dev(u))
+    assert not ctx.check_finite()
+    assert ctx.check_finite()  # the flag is cleared by the read
+    st = ctx.solve(_dev(u), raise_on_error=False)
+    assert st["status"] == bfs.BFS_ENAN
+
+
+@pytest.mark.parametrize("kprec", ["fp64", "fp32c"])
+def test_solve_small_config_matches_oracle(kprec):
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, F = W.config_small_half()
+    P = O.problem(mesh, F)
+    uref, sref = O.jfnk(P, topo, W.flat_guess(mesh), tol=1e-11)
+    assert sref["status"] == 0
+    prec = bfs.BFS_FP64 if kprec == "fp64" else bfs.BFS_FP32C
+    ctx = _ctx(mesh, topo, F, tol=1e-11, krylov_precision=prec, eta=1e-4 if kprec == "fp64" else 1e-2)
+    u = ctx.flat_guess()
+    st = ctx.solve(u)
+    print(f"solve {kprec}: {st}")
+    assert st["status"] == bfs.BFS_OK and st["fnorm_inf"] <= 1e-11
+    ug = u.cpu().numpy()
+    zg = O.nodal_values(P, ug)["zeta"]
+    zr = O.nodal_values(P, uref)["zeta"]
+    assert np.abs(zg - zr).max() <= 1e-8
+    # the oracle agrees that the GPU iterate is a root
+    assert np.abs(O.residual(P, topo, ug)).max() <= 1e-10
+
+
+def test_solve_limits_and_host_entry():
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, F = W.config_small_half()
+    ctx = _ctx(mesh, topo, F, max_newton=1, tol=1e-12)
+    st = ctx.solve(ctx.flat_guess(), raise_on_error=False)
+    assert st["status"] == bfs.BFS_ENOCONV and st["newton_its"] == 1
+    ctx2 = _ctx(mesh, topo, F, tol=1e-10)
+    uh = W.flat_guess(mesh).copy()
+    st2 = ctx2.solve_host(uh)
+    assert st2["status"] == bfs.BFS_OK
+    assert np.abs(O.residual(O.problem(mesh, F), topo, uh)).max() <= 1e-10
+    Fh = ctx2.residual_host(uh)
+    assert np.abs(Fh).max() <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# 181 x 61 (the paper-scale configuration), in the launch configuration the
+# benchmark times.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def paper_scale():
+    mesh, topo, F = W.config_paper_scale(0.7)
+    P = O.problem(mesh, F)
+    u = W.smooth_guess(mesh, 7)
+    ref, sc = O.residual(P, topo, u, with_scale=True)
+    return mesh, topo, F, P, u, ref, sc
+
+
+def test_paper_scale_residual_fp64(paper_scale):
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, F, P, u, ref, sc = paper_scale
+    ctx = _ctx(mesh, topo, F)
+    got = ctx.residual(_dev(u), precision=bfs.BFS_FP64).cpu().numpy()
+    rel = np.abs(got - ref) / (sc + 1e-300)
+    assert rel.max() <= TOL64, rel.max()
+
+
+def test_paper_scale_residual_fp32c(paper_scale):
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, F, P, u, ref, sc = paper_scale
+    ctx = _ctx(mesh, topo, F)
+    got = ctx.residual(_dev(u), precision=bfs.BFS_FP32C).cpu().numpy()
+    rel = np.abs(got - ref) / (sc + 1e-300)
+    print(f"FP32C 181x61: max |dF|/scale = {rel.max():.3e}, max |dF| = {np.abs(got - ref).max():.3e}")
+    assert rel.max() <= TOL32
+
+
+@pytest.mark.parametrize("F", [0.7, 1.5])
+def test_paper_scale_mixed_solve_is_a_root(F):
+    """Mixed-precision JFNK at 181 x 61: the converged iterate satisfies the
+    oracle's FP64 residual to the solver tolerance (a property that holds at
+    any size) and agrees with the plain FP64 solve."""
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, _ = W.config_paper_scale(F)
+    P = O.problem(mesh, F)
+    ctx = _ctx(mesh, topo, F, tol=1e-8, krylov_precision=bfs.BFS_FP32C, eta=1e-2)
+    u = ctx.flat_guess()
+    st = ctx.solve(u)
+    print(f"181x61 F={F} mixed: {st}")
+    ug = u.cpu().numpy()
+    assert np.abs(O.residual(P, topo, ug)).max() <= 1.5e-8
+    ctx64 = _ctx(mesh, topo, F, tol=1e-8)
+    u64 = ctx64.flat_guess()
+    st64 = ctx64.solve(u64)
+    print(f"181x61 F={F} fp64: {st64}")
+    z1 = O.nodal_values(P, ug)["zeta"]
+    z2 = O.nodal_values(P, u64.cpu().numpy())["zeta"]
+    assert np.abs(z1 - z2).max() <= 1e-6
