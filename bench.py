@@ -143,6 +143,53 @@ def run_reference(args):
     return 0
 
 
+def run_residual(args):
+    """Residual evaluations only (FP32C, then FP64) at 181 x 61: the pair-kernel
+    throughput part of the metric, with few launches before the first pair
+    kernel (the mode the kernel profiles are taken in)."""
+    import torch
+
+    import __graft_entry__
+    from paper_1709_08803_gb300 import bfs
+    from paper_1709_08803_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    __graft_entry__.build()
+    mesh, topo, F = W.config_paper_scale(args.F)
+    ctx = bfs.Context(mesh, topo, F)
+    u = torch.tensor(W.smooth_guess(mesh, 7), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(u)
+    res = {}
+    for name, prec in (("fp32c", bfs.BFS_FP32C), ("fp64", bfs.BFS_FP64)):
+        for _ in range(args.warmup):
+            ctx.residual(u, out, precision=prec)
+        torch.cuda.synchronize()
+        ctx.profile_read()
+        ctx.profile_enable(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            ctx.residual(u, out, precision=prec)
+        ev1.record()
+        ev1.synchronize()
+        ms64, n64, ms32, n32, _ = ctx.profile_read()
+        ctx.profile_enable(False)
+        ms = ev0.elapsed_time(ev1) / args.steps
+        kern = (ms32 / max(n32, 1)) if prec == bfs.BFS_FP32C else (ms64 / max(n64, 1))
+        res[name] = {"residual_ms": ms, "pair_kernel_ms": kern,
+                     "pair_evals_per_s": ctx.pair_evals / (ms / 1e3)}
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ach = INSTR_PER_INDEX_PAIR * mesh.n_targets * mesh.n_sources / (res["fp32c"]["pair_kernel_ms"] / 1e3) / 1e12
+    print(json.dumps({"mode": "residual", "metric": "residual pair-evals/s at 181x61", "unit": UNIT,
+                      "value": res["fp32c"]["pair_evals_per_s"], "steps": args.steps, "warmup": args.warmup,
+                      "results": res, "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                                                   "unit": "Tinst/s", "frac": ach / peak}}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -153,9 +200,13 @@ def main():
     ap.add_argument("--eta", type=float, default=1e-2)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", default="solve", choices=["solve", "residual"],
+                    help="solve: the JFNK step; residual: residual evaluations only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "residual":
+        return run_residual(args)
 
     import torch
 
