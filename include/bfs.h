@@ -29,6 +29,8 @@
 #ifndef BFS_H
 #define BFS_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -183,6 +185,36 @@ int bfs_unpack(bfs_ctx *ctx, const double *u, double *out, void *stream);
    receives the number of kernels the context has launched since bfs_setup. */
 int bfs_profile_enable(bfs_ctx *ctx, int on);
 int bfs_profile_read(bfs_ctx *ctx, double *out4, unsigned long long *launches);
+
+/* Residual for callers that cannot allocate device memory.  The paper has no
+   counterpart: this is a library convenience.  Code that runs where a device
+   allocation is not allowed (inside a host callback, under a memory pool that
+   must not grow, or without ever creating a bfs_ctx) gets the same F(u) as
+   bfs_residual, from the same kernels, with every piece of scratch kept in one
+   static device array of bfs_static_scratch_bytes() bytes (48 MiB) that each
+   GPU loading the library holds until the process exits.  No cudaMalloc,
+   cudaFree or allocating library routine is called.
+     mesh: as for bfs_setup (host struct); beta, beta_x, beta_y: DEVICE arrays
+     of N*M (index i + N*j); u, Fu: DEVICE vectors of length 3(N+1)M in the
+     layouts above; n_rad and sign_I4 as in bfs_options; precision BFS_FP64 or
+     BFS_FP32C.  Asynchronous on stream.
+   The bottom-only part of the bottom integral is recomputed on every call
+   (FP64), so a call costs about one FP64 residual more than bfs_residual.
+   Limits and errors: BFS_EINVAL (message from bfs_static_last_error) for
+   invalid arguments or a mesh whose scratch exceeds the static array (about
+   N*M <= 60000 nodes); BFS_ECUDA if the device address of the array cannot
+   be obtained.  The first call on each device looks that address up (with the
+   device current) and caches it: make that first call before any stream
+   capture.  All calls share the array, which keeps the last call's contents
+   (the NaN flag is cleared on entry; nothing else needs clearing): calls
+   that overlap on the GPU (unordered streams) race and give wrong results;
+   calls ordered in one stream are safe.  A non-finite result is not reported
+   through a context; check Fu. */
+int bfs_residual_static(const bfs_mesh *mesh, const double *beta, const double *beta_x,
+                        const double *beta_y, double F, double n_rad, double sign_I4,
+                        const double *u, double *Fu, int precision, void *stream);
+const char *bfs_static_last_error(void);
+size_t bfs_static_scratch_bytes(void);
 
 #ifdef __cplusplus
 }

@@ -95,6 +95,10 @@ def lib():
         L.bfs_residual_host.argtypes = [_VP, _VP, _VP, ctypes.c_int, _VP]
         L.bfs_flat_guess.argtypes = [_VP, _VP, _VP]
         L.bfs_unpack.argtypes = [_VP, _VP, _VP, _VP]
+        L.bfs_residual_static.argtypes = [C(bfs_mesh), _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, _VP, _VP, ctypes.c_int, _VP]
+        L.bfs_static_last_error.restype = ctypes.c_char_p
+        L.bfs_static_scratch_bytes.restype = ctypes.c_size_t
         L.bfs_profile_enable.argtypes = [_VP, ctypes.c_int]
         L.bfs_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_ulonglong)]
@@ -248,3 +252,22 @@ class Context:
         self._check(lib().bfs_unpack(self._ctx, self._vec(u), ctypes.c_void_p(_ptr(out)), _stream(stream)))
         names = ("zeta", "zeta_x", "zeta_y", "phi", "phi_x", "phi_y", "psi", "psi_x")
         return {k: out[i * NM:(i + 1) * NM].view(self.mesh.M, self.mesh.N) for i, k in enumerate(names)}
+
+
+def residual_static(mesh, beta, beta_x, beta_y, F: float, u, out=None, precision: int = BFS_FP64,
+                    n_rad: float = 0.05, sign_I4: float = -1.0, stream=None):
+    """bfs_residual_static: F(u) with no device allocation inside the call.
+    beta, beta_x, beta_y, u: float64 CUDA tensors (out too, if given)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(u)
+    for t in (beta, beta_x, beta_y, u, out):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    m = bfs_mesh(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy)
+    rc = lib().bfs_residual_static(ctypes.byref(m), ctypes.c_void_p(_ptr(beta)), ctypes.c_void_p(_ptr(beta_x)),
+                                   ctypes.c_void_p(_ptr(beta_y)), float(F), float(n_rad), float(sign_I4),
+                                   ctypes.c_void_p(_ptr(u)), ctypes.c_void_p(_ptr(out)), int(precision),
+                                   _stream(stream))
+    if rc != BFS_OK:
+        raise BfsError(rc, lib().bfs_static_last_error().decode())
+    return out
