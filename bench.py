@@ -160,7 +160,7 @@ def run_residual(args):
     u = torch.tensor(W.smooth_guess(mesh, 7), dtype=torch.float64, device="cuda")
     out = torch.empty_like(u)
     res = {}
-    for name, prec in (("fp32c", bfs.BFS_FP32C), ("fp64", bfs.BFS_FP64)):
+    for name, prec in (("fp32c", bfs.BFS_FP32C), ("df64", bfs.BFS_DF64), ("fp64", bfs.BFS_FP64)):
         for _ in range(args.warmup):
             ctx.residual(u, out, precision=prec)
         torch.cuda.synchronize()
@@ -172,10 +172,10 @@ def run_residual(args):
             ctx.residual(u, out, precision=prec)
         ev1.record()
         ev1.synchronize()
-        ms64, n64, ms32, n32, _ = ctx.profile_read()
+        prof, _ = ctx.profile_read()
         ctx.profile_enable(False)
         ms = ev0.elapsed_time(ev1) / args.steps
-        kern = (ms32 / max(n32, 1)) if prec == bfs.BFS_FP32C else (ms64 / max(n64, 1))
+        kern = prof[name][0] / max(prof[name][1], 1)
         res[name] = {"residual_ms": ms, "pair_kernel_ms": kern,
                      "pair_evals_per_s": ctx.pair_evals / (ms / 1e3)}
     peaks, src = _peaks()
@@ -253,7 +253,7 @@ def main():
     sampler.start()
     ctx.profile_read()
     ctx.profile_enable(True)
-    _, _, _, _, launches0 = ctx.profile_read()
+    _, launches0 = ctx.profile_read()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -270,7 +270,8 @@ def main():
         stats.append(st)
         evals += st["residual_evals_fp64"] + st["residual_evals_fp32"]
     torch.cuda.synchronize()
-    ms64, n64, ms32, n32, launches1 = ctx.profile_read()
+    prof, launches1 = ctx.profile_read()
+    (ms64, n64), (ms32, n32), (msdf, ndf) = prof["fp64"], prof["fp32c"], prof["df64"]
     ctx.profile_enable(False)
     clocks = sampler.stop()
     total_s = sum(step_ms) / 1e3
@@ -326,7 +327,8 @@ def main():
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz (max SM clock, {src} peaks file)",
                 "avg_launch_ms": avg32, "launches": n32,
                 "fp64_pair_kernel_avg_ms": ms64 / max(n64, 1) if n64 else None,
-                "share_of_step": (ms32 + ms64) / (total_s * 1e3) if total_s else None}
+                "df64_pair_kernel_avg_ms": msdf / max(ndf, 1) if ndf else None,
+                "share_of_step": (ms32 + ms64 + msdf) / (total_s * 1e3) if total_s else None}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -358,6 +360,7 @@ def main():
                         "d2h_bytes_per_step": 8 * ctx.n, "entry": "bfs_solve_host",
                         "steps": len(e2e_times)},
                 "gpu_launches": int(launches1 - launches0),
+                "launches_before_timed": int(launches0),
                 "clocks": clocks}
         print(json.dumps(line))
     ctx.close()

@@ -52,8 +52,11 @@ enum {
 /* Arithmetic of the boundary-integral pair sums. */
 enum {
     BFS_FP64 = 0,  /* FP64 throughout */
-    BFS_FP32C = 1  /* pair terms in FP32 with compensated (two-sum) accumulation,
+    BFS_FP32C = 1, /* pair terms in FP32 with compensated (two-sum) accumulation,
                       reduced and finished in FP64 */
+    BFS_DF64 = 2   /* pair terms in double-float arithmetic (pairs of FP32 values
+                      carrying about 46 bits) on the FP32 pipes; FP64-accurate
+                      to the 1e-10 per-row bar, reduced and finished in FP64 */
 };
 
 /* Truncated mesh x_i = x1 + (i-1) dx, i = 1..N; y_j = y1 + (j-1) dy, j = 1..M
@@ -89,6 +92,8 @@ typedef struct {
                              sqrt(eps) of the Krylov precision's arithmetic */
     double time_budget_s; /* bfs_solve wall-clock limit (<= 0: none) */
     int src_splits;       /* source splits of the pair kernels (<= 0: automatic) */
+    int outer_precision;  /* BFS_FP64 (default) or BFS_DF64 for the Newton residual
+                             and the line search */
 } bfs_options;
 
 typedef struct {
@@ -124,7 +129,7 @@ int bfs_n_unknowns(const bfs_ctx *ctx);
 double bfs_pair_evals(const bfs_ctx *ctx);
 
 /* Fu = F(u), the nonlinear residual (Sec. 3.1; App. B order).  u, Fu: device,
-   length n.  precision: BFS_FP64 or BFS_FP32C.  Asynchronous; a non-finite
+   length n.  precision: BFS_FP64, BFS_FP32C or BFS_DF64.  Asynchronous; a non-finite
    entry raises the context's NaN flag (read by bfs_check_finite). */
 int bfs_residual(bfs_ctx *ctx, const double *u, double *Fu, int precision, void *stream);
 
@@ -179,12 +184,12 @@ int bfs_unpack(bfs_ctx *ctx, const double *u, double *out, void *stream);
 
 /* Profiling.  bfs_profile_enable(ctx, 1) records a CUDA event pair on the
    launching stream around every pair-kernel launch of the context;
-   bfs_profile_read waits for the recorded events and returns, in out4,
-   {total ms FP64 pair kernels, their launch count, total ms FP32C pair
-   kernels, their launch count}, then forgets them.  *launches (optional)
+   bfs_profile_read waits for the recorded events and returns, in out6,
+   {total ms and launch count} of the FP64, FP32C and DF64 pair kernels in
+   that order, then forgets them.  *launches (optional)
    receives the number of kernels the context has launched since bfs_setup. */
 int bfs_profile_enable(bfs_ctx *ctx, int on);
-int bfs_profile_read(bfs_ctx *ctx, double *out4, unsigned long long *launches);
+int bfs_profile_read(bfs_ctx *ctx, double *out6, unsigned long long *launches);
 
 /* Residual for callers that cannot allocate device memory.  The paper has no
    counterpart: this is a library convenience.  Code that runs where a device

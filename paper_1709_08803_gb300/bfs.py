@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libbfs.so")
 BFS_OK, BFS_EINVAL, BFS_ECUDA, BFS_ENOMEM, BFS_ENAN = 0, -1, -2, -3, -4
 BFS_ENOCONV, BFS_ELINESEARCH, BFS_EBREAKDOWN, BFS_ESINGULAR = -5, -6, -7, -8
 BFS_ENOPREC, BFS_ETIMEOUT = -9, -10
-BFS_FP64, BFS_FP32C = 0, 1
+BFS_FP64, BFS_FP32C, BFS_DF64 = 0, 1, 2
 STATUS_NAMES = {0: "BFS_OK", -1: "BFS_EINVAL", -2: "BFS_ECUDA", -3: "BFS_ENOMEM", -4: "BFS_ENAN",
                 -5: "BFS_ENOCONV", -6: "BFS_ELINESEARCH", -7: "BFS_EBREAKDOWN",
                 -8: "BFS_ESINGULAR", -9: "BFS_ENOPREC", -10: "BFS_ETIMEOUT"}
@@ -49,7 +49,8 @@ class bfs_options(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("max_krylov", ctypes.c_int), ("eta", ctypes.c_double),
                 ("krylov_precision", ctypes.c_int), ("jv_h_rel", ctypes.c_double),
-                ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int)]
+                ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
+                ("outer_precision", ctypes.c_int)]
 
 
 class bfs_stats(ctypes.Structure):
@@ -239,11 +240,13 @@ class Context:
         self._check(lib().bfs_profile_enable(self._ctx, int(bool(on))))
 
     def profile_read(self):
-        """Returns (ms_fp64, launches_fp64, ms_fp32c, launches_fp32c, kernel_launches)."""
-        out = (ctypes.c_double * 4)()
+        """Returns {"fp64"|"fp32c"|"df64": (total ms, launches)} of the pair kernels
+        since the last read, and the context's kernel-launch counter."""
+        out = (ctypes.c_double * 6)()
         n = ctypes.c_ulonglong()
         self._check(lib().bfs_profile_read(self._ctx, out, ctypes.byref(n)))
-        return out[0], int(out[1]), out[2], int(out[3]), int(n.value)
+        return ({"fp64": (out[0], int(out[1])), "fp32c": (out[2], int(out[3])),
+                 "df64": (out[4], int(out[5]))}, int(n.value))
 
     def unpack(self, u, stream=None):
         import torch

@@ -30,6 +30,8 @@ void free_all(bfs_ctx *c)
     cudaFree(c->d_src32);
     cudaFree(c->d_tgt64);
     cudaFree(c->d_tgt32);
+    cudaFree(c->d_srcdf);
+    cudaFree(c->d_tgtdf);
     cudaFree(c->d_part);
     cudaFree(c->d_constB);
     cudaFree(c->d_flag);
@@ -80,6 +82,7 @@ void bfs_default_options(bfs_options *o)
     o->jv_h_rel = 0.0;
     o->time_budget_s = 0.0;
     o->src_splits = 0;
+    o->outer_precision = BFS_FP64;
 }
 
 const char *bfs_last_error(const bfs_ctx *c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -112,8 +115,10 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
         return set_err(nullptr, BFS_EINVAL, "gmres_restart must be in [1, 120]");
     if (o.sign_I4 != 1.0 && o.sign_I4 != -1.0)
         return set_err(nullptr, BFS_EINVAL, "sign_I4 must be +1 or -1");
-    if (o.krylov_precision != BFS_FP64 && o.krylov_precision != BFS_FP32C)
+    if (o.krylov_precision != BFS_FP64 && o.krylov_precision != BFS_FP32C && o.krylov_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "unknown krylov_precision");
+    if (o.outer_precision != BFS_FP64 && o.outer_precision != BFS_DF64)
+        return set_err(nullptr, BFS_EINVAL, "outer_precision must be BFS_FP64 or BFS_DF64");
     const size_t NM = (size_t)N * M;
     for (size_t q = 0; q < NM; q++) {
         if (!isfinite(topo->beta[q]) || !isfinite(topo->beta_x[q]) || !isfinite(topo->beta_y[q]))
@@ -134,8 +139,11 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     cudaGetDevice(&c->device);
     const int sms = bfs::num_sms(c->device);
     bfs::plans_for(c->Nt, c->Ns, o.src_splits, sms, &c->plan64, &c->plan32);
+    c->plandf = bfs::plan_df(c->Nt, c->Ns, o.src_splits, sms);
     c->Ns_cap = std::max(c->plan64.splits * c->plan64.per_split, c->plan32.splits * c->plan32.per_split);
-    c->part_cap = (size_t)std::max(c->plan64.splits, c->plan32.splits) * bfs::NACC * c->Nt;
+    c->Ns_cap = std::max(c->Ns_cap, c->plandf.splits * c->plandf.per_split);
+    c->part_cap = (size_t)std::max(std::max(c->plan64.splits, c->plan32.splits), c->plandf.splits) *
+                  bfs::NACC * c->Nt;
 
     auto fail = [&](int code, const std::string &m) {
         free_all(c);
@@ -153,6 +161,8 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     ALLOC(c->d_src32, sizeof(float) * bfs::REC * (size_t)c->Ns_cap);
     ALLOC(c->d_tgt64, sizeof(double) * bfs::TREC * (size_t)c->Nt);
     ALLOC(c->d_tgt32, sizeof(float) * bfs::TREC * (size_t)c->Nt);
+    ALLOC(c->d_srcdf, sizeof(float) * 32 * (size_t)c->Ns_cap);
+    ALLOC(c->d_tgtdf, sizeof(float) * 32 * (size_t)c->Nt);
     ALLOC(c->d_part, sizeof(double) * c->part_cap);
     ALLOC(c->d_constB, sizeof(double) * (size_t)c->Nt);
     ALLOC(c->d_flag, sizeof(int));
@@ -187,7 +197,8 @@ void bfs_destroy(bfs_ctx *c)
 int bfs_residual(bfs_ctx *c, const double *u, double *Fu, int precision, void *stream)
 {
     if (!c || !u || !Fu) return set_err(c, BFS_EINVAL, "NULL argument");
-    if (precision != BFS_FP64 && precision != BFS_FP32C) return set_err(c, BFS_EINVAL, "bad precision");
+    if (precision != BFS_FP64 && precision != BFS_FP32C && precision != BFS_DF64)
+        return set_err(c, BFS_EINVAL, "bad precision");
     return bfs::residual_launch(c, u, Fu, precision, (cudaStream_t)stream);
 }
 
@@ -199,6 +210,7 @@ int bfs_check_finite(bfs_ctx *c, void *stream)
     BFS_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+    if (flag & 2) return set_err(c, BFS_ETIMEOUT, "a grid barrier of the preconditioner apply timed out");
     if (flag) return set_err(c, BFS_ENAN, "a residual entry was not finite");
     return BFS_OK;
 }
@@ -207,7 +219,8 @@ int bfs_jvp(bfs_ctx *c, const double *u, const double *Fu, const double *z, doub
             int precision, void *stream)
 {
     if (!c || !u || !Fu || !z || !Jz) return set_err(c, BFS_EINVAL, "NULL argument");
-    if (precision != BFS_FP64 && precision != BFS_FP32C) return set_err(c, BFS_EINVAL, "bad precision");
+    if (precision != BFS_FP64 && precision != BFS_FP32C && precision != BFS_DF64)
+        return set_err(c, BFS_EINVAL, "bad precision");
     return bfs::jvp_launch(c, u, Fu, z, Jz, h, precision, (cudaStream_t)stream);
 }
 
@@ -303,19 +316,19 @@ int bfs_profile_enable(bfs_ctx *c, int on)
     return BFS_OK;
 }
 
-int bfs_profile_read(bfs_ctx *c, double *out4, unsigned long long *launches)
+int bfs_profile_read(bfs_ctx *c, double *out6, unsigned long long *launches)
 {
     if (!c) return BFS_EINVAL;
     if (launches) *launches = c->launches;
-    if (!out4) return BFS_OK;
-    out4[0] = out4[1] = out4[2] = out4[3] = 0.0;
+    if (!out6) return BFS_OK;
+    for (int i = 0; i < 6; i++) out6[i] = 0.0;
     for (size_t i = 0; i < c->ev_kind.size(); i++) {
         float ms = 0.0f;
         BFS_CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[2 * i + 1]));
         BFS_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
         int k = c->ev_kind[i];
-        out4[2 * k] += ms;
-        out4[2 * k + 1] += 1.0;
+        out6[2 * k] += ms;
+        out6[2 * k + 1] += 1.0;
     }
     c->ev_used = 0;
     c->ev_kind.clear();

@@ -67,7 +67,9 @@ struct bfs_ctx {
     double *d_part;                // max splits * NACC * Nt
     double *d_constB;              // Nt: bottom-only single-layer part at bottom targets
     int *d_flag;                   // non-finite flag
-    bfs::PairPlan plan64, plan32;
+    float *d_srcdf;                // Ns_cap * 32 double-float source records
+    float *d_tgtdf;                // Nt * 32 double-float target records
+    bfs::PairPlan plan64, plan32, plandf;
     size_t part_cap;
 
     // Jacobian-vector product scratch
@@ -85,7 +87,7 @@ struct bfs_ctx {
     double *h_pin;    // pinned host scalars
 
     // preconditioner
-    int pc_ready, pc_h, nb;
+    int pc_ready, pc_h, nb, apply_grid;
     double *d_pc;      // M * (2h+1) * nb * nb  block-banded factors
     double *d_gj;      // 2 * nb * 2nb  Gauss-Jordan ping-pong
     double *d_rowsum5; // Nt
@@ -111,9 +113,13 @@ int constB_launch(bfs_ctx *c, cudaStream_t s);
 PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, int sms);
 void plans_for(int Nt, int Ns, int splits_req, int sms, PairPlan *p64, PairPlan *p32);
 
+// pairs_df64.cu
+PairPlan plan_df(int Nt, int Ns, int splits_req, int sms);
+int pairs_df_launch(bfs_ctx *c, cudaStream_t s);
+
 // solver.cu
 int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
-               double h, int precision, cudaStream_t s);
+               double h, int precision, cudaStream_t s, bool unorm_ready = false);
 int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s);
 int alloc_solver(bfs_ctx *c);
 void norms_launch(bfs_ctx *c, const double *v, int n, double *d_out2, double *d_outinf, cudaStream_t s);

@@ -182,8 +182,6 @@ __global__ void k_form_sparse(PcArgs a, double *pc)
 // Gauss-Jordan inversion with partial pivoting of one nb x nb block, one launch
 // per pivot column on ping-pong buffers X = [D | I] (nb x 2nb, row-major).
 // ---------------------------------------------------------------------------
-constexpr int GJ_ROWS = 4;
-
 __global__ void k_gj_load(const double *__restrict__ D, double *__restrict__ X, int nb)
 {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * 2 * nb;
@@ -193,63 +191,73 @@ __global__ void k_gj_load(const double *__restrict__ D, double *__restrict__ X, 
     }
 }
 
-__global__ void k_gj_step(const double *__restrict__ Xi, double *__restrict__ Xo, int nb, int c,
-                          int *flag)
-{
-    __shared__ double bv[32];
-    __shared__ int bi[32];
-    __shared__ int piv;
-    __shared__ double pval;
-    const int ld = 2 * nb;
-    // pivot search in column c, rows c..nb-1 (every CTA, same order -> same answer)
-    double best = -1.0;
-    int bidx = c;
-    for (int r = c + threadIdx.x; r < nb; r += blockDim.x) {
-        double v = fabs(Xi[(size_t)r * ld + c]);
-        if (v > best) { best = v; bidx = r; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, best, o);
-        int oi = __shfl_down_sync(0xffffffffu, bidx, o);
-        if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = bv[0];
-        int i = bi[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-            if (bv[w] > b || (bv[w] == b && bi[w] < i)) { b = bv[w]; i = bi[w]; }
-        piv = i;
-        pval = Xi[(size_t)i * ld + c];
-        if (!(b > 0.0) && blockIdx.x == 0) atomicOr(flag, 1);
-    }
-    __syncthreads();
-    const int p = piv;
-    const double ip = pval != 0.0 ? 1.0 / pval : 0.0;
-    const int r0 = blockIdx.x * GJ_ROWS;
-    for (int rr = 0; rr < GJ_ROWS; rr++) {
-        int r = r0 + rr;
-        if (r >= nb) break;
-        int src = (r == c) ? p : ((r == p) ? c : r);
-        const double *xs = Xi + (size_t)src * ld;
-        const double *xp = Xi + (size_t)p * ld;
-        double *xo = Xo + (size_t)r * ld;
-        if (r == c) {
-            for (int q = c + threadIdx.x; q < ld; q += blockDim.x) xo[q] = xp[q] * ip;
-        } else {
-            const double f = xs[c] * ip;
-            for (int q = c + threadIdx.x; q < ld; q += blockDim.x) xo[q] = fma(-f, xp[q], xs[q]);
-        }
-    }
-}
-
 __global__ void k_gj_store(const double *__restrict__ X, double *__restrict__ D, int nb)
 {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
          e += (size_t)gridDim.x * blockDim.x) {
         int r = (int)(e / nb), c = (int)(e % nb);
         D[e] = X[(size_t)r * 2 * nb + nb + c];
+    }
+}
+
+// Cooperative form of the same inversion: one launch per diagonal block, a
+// bounded grid barrier between pivot columns (see grid_sync below).
+struct CoopBar;
+__device__ bool grid_sync(CoopBar *b, int *flag);
+
+__global__ void __launch_bounds__(256) k_gj_coop(double *X0, double *X1, int nb, int *pivflag,
+                                                 CoopBar *bar, int *flag)
+{
+    __shared__ double bv[8];
+    __shared__ int bi[8];
+    __shared__ int piv;
+    __shared__ double pval;
+    const int ld = 2 * nb;
+    const double *Xi = X0;
+    double *Xo = X1;
+    for (int c = 0; c < nb; c++) {
+        double best = -1.0;
+        int bidx = c;
+        for (int r = c + threadIdx.x; r < nb; r += blockDim.x) {
+            double v = fabs(__ldcg(Xi + (size_t)r * ld + c));
+            if (v > best) { best = v; bidx = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_down_sync(0xffffffffu, best, o);
+            int oi = __shfl_down_sync(0xffffffffu, bidx, o);
+            if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = bv[0];
+            int i = bi[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+                if (bv[w] > b || (bv[w] == b && bi[w] < i)) { b = bv[w]; i = bi[w]; }
+            piv = i;
+            pval = __ldcg(Xi + (size_t)i * ld + c);
+            if (!(b > 0.0) && blockIdx.x == 0) atomicOr(pivflag, 1);
+        }
+        __syncthreads();
+        const int p = piv;
+        const double ip = pval != 0.0 ? 1.0 / pval : 0.0;
+        for (int r = blockIdx.x; r < nb; r += gridDim.x) {
+            const int src = (r == c) ? p : ((r == p) ? c : r);
+            const double *xs = Xi + (size_t)src * ld;
+            const double *xp = Xi + (size_t)p * ld;
+            double *xo = Xo + (size_t)r * ld;
+            if (r == c) {
+                for (int q = c + threadIdx.x; q < ld; q += blockDim.x) __stcg(xo + q, __ldcg(xp + q) * ip);
+            } else {
+                const double f = __ldcg(xs + c) * ip;
+                for (int q = c + threadIdx.x; q < ld; q += blockDim.x)
+                    __stcg(xo + q, fma(-f, __ldcg(xp + q), __ldcg(xs + q)));
+            }
+        }
+        if (!grid_sync(bar, flag)) return;
+        const double *t = Xi;
+        Xi = Xo;
+        Xo = const_cast<double *>(t);
     }
 }
 
@@ -331,50 +339,139 @@ static int gemm_batch(bfs_ctx *c, std::vector<const double *> &A, std::vector<co
 }
 
 // ---------------------------------------------------------------------------
-// Apply: permutations between the order of u / F and the slice-interleaved order,
-// and one block-row GEMV per slice for each triangular sweep.
+// One cooperative launch per apply: permutation in, forward sweep, backward
+// sweep, permutation out, with a grid barrier between dependent slices.  The
+// launch is cooperative, so every block is resident and the barrier always
+// completes; its spin is still bounded (about one second), after which the
+// kernel raises bit 2 of the context flag and returns.
 // ---------------------------------------------------------------------------
-__global__ void k_perm_in(const double *__restrict__ r, double *__restrict__ x, int NB, int M)
-{
-    int n = 3 * NB * M;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
-        x[(size_t)l * 3 * NB + g * NB + p] = r[e];
-    }
-}
-
-__global__ void k_perm_out(const double *__restrict__ x, double *__restrict__ z, int NB, int M)
-{
-    int n = 3 * NB * M;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
-        z[e] = x[(size_t)l * 3 * NB + g * NB + p];
-    }
-}
-
-struct SweepArgs {
-    const double *blk[17];  // up to h + 1 blocks (h <= 16)
-    const double *vec[17];
-    double sgn[17];
-    int cnt;
+struct CoopBar {
+    unsigned int count;
+    unsigned int gen;
 };
 
-// out[r] = (base ? base[r] : 0) + sum_b sgn_b (blk_b row r) . vec_b   (one warp per row)
-__global__ void k_sweep(SweepArgs sa, const double *__restrict__ base, double *__restrict__ out,
-                        int nb)
+__device__ bool grid_sync(CoopBar *b, int *flag)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= nb) return;
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = &b->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&b->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned int spins = 0;
+            while (*vgen == g) {
+                if (++spins > (1u << 24)) {
+                    atomicOr(flag, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok;
+}
+
+struct ApplyArgs {
+    const double *pc;
+    const double *r;
+    double *z, *x, *y;
+    int nb, NB, M, h;
+    CoopBar *bar;
+    int *flag;
+};
+
+constexpr int AP_TPB = 256;
+
+// sum over blocks b of sgn_b * (row `row` of block b) . vec_b, split over the
+// 8 warps of the CTA by column ranges; returned to thread 0
+template <int MAXB>
+__device__ __forceinline__ double row_dots(const double *const *blk, const double *const *vec,
+                                           const double *sgn, int cnt, int row, int nb, double *red)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cw = (nb + (AP_TPB / 32) - 1) / (AP_TPB / 32);
+    const int c0 = warp * cw, c1 = min(nb, c0 + cw);
     double acc = 0.0;
-    for (int b = 0; b < sa.cnt; b++) {
-        const double *row = sa.blk[b] + (size_t)warp * nb;
-        const double *v = sa.vec[b];
+    for (int b = 0; b < cnt; b++) {
+        const double *rp = blk[b] + (size_t)row * nb;
+        const double *v = vec[b];
         double t = 0.0;
-        for (int q = lane; q < nb; q += 32) t = fma(row[q], v[q], t);
-        acc = fma(sa.sgn[b], t, acc);
+        for (int c = c0 + lane; c < c1; c += 32) t = fma(__ldg(rp + c), __ldcg(v + c), t);
+        acc = fma(sgn[b], t, acc);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[warp] = (base ? base[warp] : 0.0) + acc;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < AP_TPB / 32; w++) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(AP_TPB) k_apply_coop(ApplyArgs a)
+{
+    __shared__ double red[AP_TPB / 32];
+    const int nb = a.nb, NB = a.NB, M = a.M, h = a.h, nd = 2 * h + 1;
+    const size_t bsz = (size_t)nb * nb;
+    const int n = 3 * NB * M;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    for (int e = gtid; e < n; e += gstride) {
+        int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
+        __stcg(a.x + (size_t)l * nb + g * NB + p, a.r[e]);
+    }
+    if (!grid_sync(a.bar, a.flag)) return;
+    const double *blk[17];
+    const double *vec[17];
+    double sgn[17];
+    // forward: y_k = x_k - sum_{i<k} L_ki y_i
+    for (int k = 0; k < M; k++) {
+        int cnt = 0;
+        for (int i = max(0, k - h); i < k; i++) {
+            blk[cnt] = a.pc + ((size_t)k * nd + (i - k + h)) * bsz;
+            vec[cnt] = a.y + (size_t)i * nb;
+            sgn[cnt] = -1.0;
+            cnt++;
+        }
+        for (int row = blockIdx.x; row < nb; row += gridDim.x) {
+            double s = row_dots<17>(blk, vec, sgn, cnt, row, nb, red);
+            if (threadIdx.x == 0) __stcg(a.y + (size_t)k * nb + row, __ldcg(a.x + (size_t)k * nb + row) + s);
+        }
+        if (!grid_sync(a.bar, a.flag)) return;
+    }
+    // backward: x_k = D_k^-1 y_k - sum_{j>k} W_kj x_j
+    for (int k = M - 1; k >= 0; k--) {
+        int cnt = 0;
+        blk[cnt] = a.pc + ((size_t)k * nd + h) * bsz;
+        vec[cnt] = a.y + (size_t)k * nb;
+        sgn[cnt] = 1.0;
+        cnt++;
+        for (int j = k + 1; j <= min(M - 1, k + h); j++) {
+            blk[cnt] = a.pc + ((size_t)k * nd + (j - k + h)) * bsz;
+            vec[cnt] = a.x + (size_t)j * nb;
+            sgn[cnt] = -1.0;
+            cnt++;
+        }
+        for (int row = blockIdx.x; row < nb; row += gridDim.x) {
+            double s = row_dots<17>(blk, vec, sgn, cnt, row, nb, red);
+            if (threadIdx.x == 0) __stcg(a.x + (size_t)k * nb + row, s);
+        }
+        if (!grid_sync(a.bar, a.flag)) return;
+    }
+    for (int e = gtid; e < n; e += gstride) {
+        int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
+        a.z[e] = __ldcg(a.x + (size_t)l * nb + g * NB + p);
+    }
 }
 
 static PcArgs pc_args(const bfs_ctx *c, int h)
@@ -418,11 +515,11 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     }
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_gj, sizeof(double) * (bsz * 4 + bsz * (size_t)(h > 0 ? h : 1))));
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_rowsum5, sizeof(double) * (size_t)c->Nt));
-    BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int)));
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int) * 8));  // [0] pivot flag, [4..5] grid barrier
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_perm_a, sizeof(double) * 2 * (size_t)c->n));
     c->d_perm_b = c->d_perm_a + c->n;
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_pc, 0, sizeof(double) * bsz * M * nd, s));
-    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_pivflag, 0, sizeof(int), s));
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_pivflag, 0, sizeof(int) * 8, s));
 
     PcArgs a = pc_args(c, h);
     k_rowsum5<<<(c->Nt + 127) / 128, 128, 0, s>>>(a, c->d_rowsum5);
@@ -436,17 +533,29 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
 
     auto B = [&](int l, int m) { return c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz; };
     double *X0 = c->d_gj, *X1 = c->d_gj + 2 * bsz, *tmp = c->d_gj + 4 * bsz;
-    const int gj_blocks = (nb + GJ_ROWS - 1) / GJ_ROWS;
+    int gj_per_sm = 0;
+    BFS_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gj_per_sm, k_gj_coop, 256, 0));
+    if (gj_per_sm < 1) {
+        c->err = "Gauss-Jordan kernel cannot be resident";
+        return BFS_ECUDA;
+    }
+    const int gj_grid = std::min(num_sms(c->device) * std::min(gj_per_sm, 2), nb);
     for (int k = 0; k < M; k++) {
         // D_k^-1 in place
         k_gj_load<<<512, 256, 0, s>>>(B(k, k), X0, nb);
         c->launches++;
-        double *xi = X0, *xo = X1;
-        for (int col = 0; col < nb; col++) {
-            k_gj_step<<<gj_blocks, 256, 0, s>>>(xi, xo, nb, col, c->d_pivflag);
+        {
+            CoopBar *bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
+            BFS_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+            double *x0 = X0, *x1 = X1;
+            int nbv = nb;
+            int *pf = c->d_pivflag, *fl = c->d_flag;
+            void *args[] = {&x0, &x1, &nbv, &pf, &bar, &fl};
+            BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(gj_grid), dim3(256),
+                                                        args, 0, s));
             c->launches++;
-            std::swap(xi, xo);
         }
+        double *xi = (nb % 2 == 0) ? X0 : X1;  // after nb ping-pong steps
         k_gj_store<<<512, 256, 0, s>>>(xi, B(k, k), nb);
         c->launches++;
         const int hi = std::min(M - 1, k + h);
@@ -491,38 +600,25 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
         c->err = "preconditioner applied before bfs_precond_factor";
         return BFS_ENOPREC;
     }
-    const int nb = c->nb, M = c->M, h = c->pc_h, nd = 2 * h + 1, NB = c->N + 1;
-    const size_t bsz = (size_t)nb * nb;
-    double *x = c->d_perm_a, *y = c->d_perm_b;
-    const int g = (c->n + 255) / 256;
-    k_perm_in<<<g, 256, 0, s>>>(r, x, NB, M);
-    c->launches++;
-    auto B = [&](int l, int m) { return (const double *)(c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz); };
-    const int sweep_blocks = (nb * 32 + 255) / 256;
-    // forward: y_k = x_k - sum_{i<k} L_ki y_i  (in place in y)
-    for (int k = 0; k < M; k++) {
-        SweepArgs sa;
-        sa.cnt = 0;
-        for (int i = std::max(0, k - h); i < k; i++) {
-            sa.blk[sa.cnt] = B(k, i); sa.vec[sa.cnt] = y + (size_t)i * nb; sa.sgn[sa.cnt] = -1.0; sa.cnt++;
+    if (c->apply_grid <= 0) {
+        int per_sm = 0;
+        BFS_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_coop, AP_TPB, 0));
+        if (per_sm < 1) {
+            c->err = "apply kernel cannot be resident";
+            return BFS_ECUDA;
         }
-        k_sweep<<<sweep_blocks, 256, 0, s>>>(sa, x + (size_t)k * nb, y + (size_t)k * nb, nb);
-        c->launches++;
+        c->apply_grid = num_sms(c->device) * std::min(per_sm, 4);
     }
-    // backward: x_k = D_k^-1 y_k - sum_{j>k} W_kj x_j  (result in x)
-    for (int k = M - 1; k >= 0; k--) {
-        SweepArgs sa;
-        sa.cnt = 0;
-        sa.blk[sa.cnt] = B(k, k); sa.vec[sa.cnt] = y + (size_t)k * nb; sa.sgn[sa.cnt] = 1.0; sa.cnt++;
-        for (int j = k + 1; j <= std::min(M - 1, k + h); j++) {
-            sa.blk[sa.cnt] = B(k, j); sa.vec[sa.cnt] = x + (size_t)j * nb; sa.sgn[sa.cnt] = -1.0; sa.cnt++;
-        }
-        k_sweep<<<sweep_blocks, 256, 0, s>>>(sa, nullptr, x + (size_t)k * nb, nb);
-        c->launches++;
-    }
-    k_perm_out<<<g, 256, 0, s>>>(x, z, NB, M);
+    ApplyArgs a;
+    a.pc = c->d_pc; a.r = r; a.z = z; a.x = c->d_perm_a; a.y = c->d_perm_b;
+    a.nb = c->nb; a.NB = c->N + 1; a.M = c->M; a.h = c->pc_h;
+    a.bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
+    a.flag = c->d_flag;
+    BFS_CUDA_TRY(c, cudaMemsetAsync(a.bar, 0, sizeof(CoopBar), s));
+    void *args[] = {&a};
+    BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_apply_coop, dim3(c->apply_grid),
+                                                dim3(AP_TPB), args, 0, s));
     c->launches++;
-    BFS_CUDA_TRY(c, cudaGetLastError());
     return BFS_OK;
 }
 

@@ -23,22 +23,29 @@ namespace bfs {
 __global__ void k_unpack(const double *__restrict__ u, double *__restrict__ nodal, int N, int M,
                          double dx)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * M) return;
-    int f = t / M, j = t - f * M;
-    size_t NM = (size_t)N * M;
+    // one warp per (field, slice): inclusive shuffle scan of the trapezoid increments
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= 3 * M) return;
+    const int f = warp / M, j = warp - f * M;
+    const size_t NM = (size_t)N * M;
     const double *s = u + (size_t)f * (N + 1) * M + (size_t)j * (N + 1);
     double *q = nodal + (size_t)(3 * f) * NM + (size_t)j * N;
     double *qx = nodal + (size_t)(3 * f + 1) * NM + (size_t)j * N;
-    double prev = s[0], prevx = s[1];
-    q[0] = prev;
-    qx[0] = prevx;
-    for (int i = 1; i < N; i++) {
-        double cur = s[1 + i];
-        prev = prev + 0.5 * dx * (prevx + cur);
-        q[i] = prev;
-        qx[i] = cur;
-        prevx = cur;
+    double carry = s[0];
+    for (int i0 = 0; i0 < N; i0 += 32) {
+        const int i = i0 + lane;
+        const double cur = i < N ? s[1 + i] : 0.0;
+        double inc = (i >= 1 && i < N) ? 0.5 * dx * (s[i] + cur) : 0.0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const double val = carry + inc;
+        if (i < N) {
+            q[i] = val;
+            qx[i] = cur;
+        }
+        carry = __shfl_sync(0xffffffffu, val, 31);
     }
 }
 
@@ -107,7 +114,7 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
             r[11] = w2 * a.sigma * bx[q];
             r[12] = w1;
             r[13] = w2;
-            r[14] = 0.0;
+            r[14] = ysg * j - a.jc;  // row coordinate in mesh units (exact)
             r[15] = 0.0;
         } else {  // padding: far away, zero weight
             for (int k = 0; k < REC; k++) r[k] = 0.0;
@@ -147,7 +154,7 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
     r[12] = (bs + 1.0) / a.dx - 1.0 / a.dx;
     r[13] = pxs;
     r[14] = pys;
-    r[15] = 0.0;
+    r[15] = (double)l - a.jc;  // row coordinate in mesh units (exact)
     for (int q = 0; q < TREC; q++) {
         tgt64[(size_t)e * TREC + q] = r[q];
         tgt32[(size_t)e * TREC + q] = (float)r[q];
@@ -174,26 +181,26 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
     lo += err;
 }
 
+// One tile of the all-pairs sum: targets [tile * TPB * TPT, +TPB * TPT) against
+// the sources of split `split`; writes that split's partial sums.
 template <typename R, int TPB, int TPT, int CH, bool COMP>
-__global__ void __launch_bounds__(TPB)
-k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int Nt,
-        double *__restrict__ part)
+__device__ __forceinline__ void pair_tile(const R *__restrict__ src, int per_split,
+                                          const R *__restrict__ tgt, int Nt,
+                                          double *__restrict__ part, int tile, int split, R *sh)
 {
     typedef typename Vec<R>::T V;
     constexpr int VW = Vec<R>::W;
-    __shared__ __align__(16) R sh[CH * REC];
-    const int split = blockIdx.y;
     const R *sb = src + (size_t)split * per_split * REC;
 
-    R tx[TPT], ty[TPT], tz[TPT], tB[TPT], tzx[TPT], tf[TPT], tg[TPT];
+    R tx[TPT], ty[TPT], tz[TPT], tB[TPT], tf[TPT], tg[TPT];
     R cA[TPT], cB[TPT], cC[TPT], cTB[TPT], cBT[TPT];
     int tid[TPT];
 #pragma unroll
     for (int p = 0; p < TPT; p++) {
-        int t = blockIdx.x * TPB * TPT + p * TPB + threadIdx.x;
+        int t = tile * TPB * TPT + p * TPB + threadIdx.x;
         tid[p] = t;
         const R *tr = tgt + (size_t)min(t, Nt - 1) * TREC;
-        tx[p] = tr[0]; ty[p] = tr[1]; tz[p] = tr[2]; tB[p] = tr[3]; tzx[p] = tr[4];
+        tx[p] = tr[0]; ty[p] = tr[1]; tz[p] = tr[2]; tB[p] = tr[3];
         tf[p] = tr[6]; tg[p] = tr[7]; cA[p] = tr[8]; cB[p] = tr[9]; cC[p] = tr[10];
         cTB[p] = tr[11]; cBT[p] = tr[12];
     }
@@ -284,6 +291,15 @@ k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int
     }
 }
 
+template <typename R, int TPB, int TPT, int CH, bool COMP>
+__global__ void __launch_bounds__(TPB)
+k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int Nt,
+        double *__restrict__ part)
+{
+    __shared__ __align__(16) R sh[CH * REC];
+    pair_tile<R, TPB, TPT, CH, COMP>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, sh);
+}
+
 // ---------------------------------------------------------------------------
 // Closed-form integral of S2 = (A s^2 + B s t + C t^2)^(-1/2) over a rectangle
 // (Sec. 3.1).  The antiderivative printed in the paper is
@@ -320,30 +336,48 @@ struct FinArgs {
     double x1, y1, dx, dy, ylo, yhi, xhi, F, n_rad;
 };
 
-// F2 / F7 / F1 at every half point, radiation rows per slice.
+// F2 / F7 / F1 at every half point (four lanes per target: the split partial
+// sums and the four corners of the closed-form integral are spread over the
+// lanes), radiation rows per slice.
 __global__ void k_finish(const double *__restrict__ part, const double *__restrict__ tgt,
                          const double *__restrict__ constB, const double *__restrict__ nodal,
                          double *__restrict__ Fu, int *__restrict__ flag, FinArgs a)
 {
     const double TWO_PI = 6.283185307179586476925286766559;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = g >> 2, q4 = g & 3;
     const int N = a.N, M = a.M;
     const size_t blk = (size_t)(N + 1) * M;
     bool bad = false;
-    if (e < a.Nt) {
-        int k = e % (N - 1), l = e / (N - 1);
-        double acc[NACC];
+    const bool is_t = e < a.Nt;
+    const int et = is_t ? e : 0;
+    double acc[NACC];
 #pragma unroll
-        for (int q = 0; q < NACC; q++) acc[q] = 0.0;
-        for (int s = 0; s < a.splits; s++)
+    for (int q = 0; q < NACC; q++) acc[q] = 0.0;
+    if (is_t) {
+#pragma unroll 4
+        for (int s = q4; s < a.splits; s += 4)
 #pragma unroll
-            for (int q = 0; q < NACC; q++) acc[q] += part[((size_t)s * NACC + q) * a.Nt + e];
-        const double *r = tgt + (size_t)e * TREC;
+            for (int q = 0; q < NACC; q++) acc[q] += part[((size_t)s * NACC + q) * a.Nt + et];
+    }
+    const int k = et % (N - 1), l = et / (N - 1);
+    const double *r = tgt + (size_t)et * TREC;
+    const double A = r[8], B = r[9], C = r[10];
+    const double xs = a.x1 + (k + 0.5) * a.dx, ys = a.y1 + l * a.dy;
+    // corner q4 of the rectangle: (s2,t2) +, (s1,t2) -, (s2,t1) -, (s1,t1) +
+    const double sc = (q4 & 1) ? a.x1 - xs : a.xhi - xs;
+    const double tc = (q4 & 2) ? a.ylo - ys : a.yhi - ys;
+    double g2 = (is_t ? antideriv_S2(A, B, C, sc, tc) : 0.0) * (((q4 == 1) || (q4 == 2)) ? -1.0 : 1.0);
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+#pragma unroll
+        for (int q = 0; q < NACC; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    }
+    if (is_t && q4 == 0) {
         const double zs = r[2] * a.dx, zxs = r[4], zys = r[5], fs = r[6], gs = r[7];
-        const double A = r[8], B = r[9], C = r[10], pxs = r[13], pys = r[14];
-        const double xs = a.x1 + (k + 0.5) * a.dx, ys = a.y1 + l * a.dy;
-        const double I2pp = rect_S2(A, B, C, a.x1 - xs, a.xhi - xs, a.ylo - ys, a.yhi - ys);
-        const double F2 = acc[0] + acc[1] - zxs * acc[2] + zxs * I2pp - TWO_PI * fs;
+        const double pxs = r[13], pys = r[14];
+        const double F2 = acc[0] + acc[1] - zxs * acc[2] + zxs * g2 - TWO_PI * fs;
         const double F7 = acc[3] + acc[4] + constB[e] - TWO_PI * gs;
         const double num = (1.0 + zxs * zxs) * pys * pys + (1.0 + zys * zys) * pxs * pxs -
                            2.0 * zxs * zys * pxs * pys;
@@ -353,15 +387,15 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
         Fu[blk + row] = F2;
         Fu[2 * blk + row] = F7;
         bad = !isfinite(F1) || !isfinite(F2) || !isfinite(F7);
-    } else if (e < a.Nt + M) {
+    } else if (!is_t && q4 == 0 && e < a.Nt + M) {
         // radiation conditions of Scullen at x1 (Sec. 3.1); second derivatives
         // are forward differences of the first derivatives
-        int l = e - a.Nt;
-        const size_t NM = (size_t)N * M, q = (size_t)l * N, row = (size_t)l * (N + 1);
+        const int lsl = e - a.Nt;
+        const size_t NM = (size_t)N * M, qq = (size_t)lsl * N, row = (size_t)lsl * (N + 1);
         const double x1 = a.x1, n = a.n_rad, h = a.dx;
         for (int f = 0; f < 3; f++) {
-            const double v1 = nodal[(3 * f) * NM + q];
-            const double d1 = nodal[(3 * f + 1) * NM + q], d2 = nodal[(3 * f + 1) * NM + q + 1];
+            const double v1 = nodal[(3 * f) * NM + qq];
+            const double d1 = nodal[(3 * f + 1) * NM + qq], d2 = nodal[(3 * f + 1) * NM + qq + 1];
             double Fa, Fb;
             if (f == 0) {
                 Fa = x1 * d1 + n * v1;
@@ -448,7 +482,7 @@ PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, 
 
 int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s)
 {
-    k_unpack<<<(3 * c->M + 127) / 128, 128, 0, s>>>(u, c->d_nodal, c->N, c->M, c->dx);
+    k_unpack<<<(3 * c->M * 32 + 127) / 128, 128, 0, s>>>(u, c->d_nodal, c->N, c->M, c->dx);
     c->launches++;
     RecArgs ra = rec_args(c);
     int tot = c->Ns_cap + c->Nt;
@@ -467,25 +501,27 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
 {
     int rc = unpack_launch(c, u, s);
     if (rc) return rc;
-    const PairPlan &p = precision == BFS_FP32C ? c->plan32 : c->plan64;
+    const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
     dim3 grid(p.tiles, p.splits);
     cudaEvent_t ev1 = nullptr;
     if (c->prof_on) {
         cudaEvent_t ev0 = prof_event(c);
         ev1 = prof_event(c);
-        c->ev_kind.push_back(precision == BFS_FP32C ? 1 : 0);
+        c->ev_kind.push_back(precision == BFS_FP32C ? 1 : (precision == BFS_DF64 ? 2 : 0));
         cudaEventRecord(ev0, s);
     }
-    if (precision == BFS_FP32C)
+    if (precision == BFS_DF64) {
+        if ((rc = pairs_df_launch(c, s))) return rc;
+    } else if (precision == BFS_FP32C)
         k_pairs<float, P32_TPB, P32_TPT, P32_CH, true>
             <<<grid, P32_TPB, 0, s>>>(c->d_src32, p.per_split, c->d_tgt32, c->Nt, c->d_part);
     else
         k_pairs<double, P64_TPB, P64_TPT, P64_CH, false>
             <<<grid, P64_TPB, 0, s>>>(c->d_src64, p.per_split, c->d_tgt64, c->Nt, c->d_part);
-    c->launches++;
+    if (precision != BFS_DF64) c->launches++;
     if (ev1) cudaEventRecord(ev1, s);
     FinArgs fa = fin_args(c, p.splits);
-    int tot = c->Nt + c->M;
+    int tot = 4 * (c->Nt + c->M);
     k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, Fu,
                                                c->d_flag, fa);
     c->launches++;

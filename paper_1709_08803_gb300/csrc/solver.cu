@@ -150,13 +150,13 @@ __global__ void k_jv_diff(double *__restrict__ Jz, const double *__restrict__ Fp
 static int grid_for(int n) { return (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184; }
 
 int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
-               double h, int precision, cudaStream_t s)
+               double h, int precision, cudaStream_t s, bool unorm_ready)
 {
     const int n = c->n;
     double h_rel = c->opt.jv_h_rel;
     if (!(h_rel > 0.0)) h_rel = precision == BFS_FP32C ? 3.4526698e-4 : 1.4901161193847656e-8;
     if (!(h > 0.0)) {
-        norms_launch(c, u, n, c->d_scal + 0, nullptr, s);
+        if (!unorm_ready) norms_launch(c, u, n, c->d_scal + 0, nullptr, s);
         norms_launch(c, z, n, c->d_scal + 1, nullptr, s);
     }
     k_jv_step<<<1, 1, 0, s>>>(c->d_scal, h, h_rel);
@@ -304,6 +304,7 @@ static int gmres(bfs_ctx *c, const double *u, const double *F, const double *Fba
     const size_t ldv = (size_t)n;
     int its = 0, rc;
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_du, 0, sizeof(double) * n, s));
+    norms_launch(c, u, n, c->d_scal + 0, nullptr, s);  // |u| is fixed during the solve
     // r = -F
     k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, F, n, -1.0, 0.0, nullptr);
     c->launches++;
@@ -325,7 +326,7 @@ static int gmres(bfs_ctx *c, const double *u, const double *F, const double *Fba
             double *vj = c->d_V + (size_t)j * ldv;
             if ((rc = precond_apply(c, vj, c->d_z, s))) return rc;
             (*precs)++;
-            if ((rc = jvp_launch(c, u, Fbase, c->d_z, c->d_w, 0.0, c->opt.krylov_precision, s))) return rc;
+            if ((rc = jvp_launch(c, u, Fbase, c->d_z, c->d_w, 0.0, c->opt.krylov_precision, s, true))) return rc;
             (*jvs)++;
             arnoldi_orth(c, j + 1, s);
             k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V + (size_t)(j + 1) * ldv, c->d_w, n,
@@ -351,7 +352,7 @@ static int gmres(bfs_ctx *c, const double *u, const double *F, const double *Fba
         c->launches++;
         if (res <= target || its >= maxit) break;
         // restart: r = -F - J du
-        if ((rc = jvp_launch(c, u, Fbase, c->d_du, c->d_w, 0.0, c->opt.krylov_precision, s))) return rc;
+        if ((rc = jvp_launch(c, u, Fbase, c->d_du, c->d_w, 0.0, c->opt.krylov_precision, s, true))) return rc;
         (*jvs)++;
         k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, c->d_w, n, -1.0, -1.0, nullptr);
         c->launches++;
@@ -379,7 +380,8 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         if (st) *st = S;
         return status;
     };
-    if ((rc = residual_launch(c, u, c->d_F, BFS_FP64, s))) return finish(rc);
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+    if ((rc = residual_launch(c, u, c->d_F, c->opt.outer_precision, s))) return finish(rc);
     S.residual_evals_fp64++;
     norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
     if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
@@ -404,12 +406,21 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         rc = gmres(c, u, c->d_F, Fbase, f2, c->opt.eta, c->opt.max_krylov, &its, &precs, &jvs, s);
         S.krylov_its += its;
         if (rc) return finish(rc);
+        {
+            int fl = 0;
+            BFS_CUDA_TRY(c, cudaMemcpyAsync(&fl, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (fl & 2) {
+                c->err = "a grid barrier of the preconditioner apply timed out";
+                return finish(BFS_ETIMEOUT);
+            }
+        }
         double mu = 1.0;
         bool ok = false;
         while (mu >= 1e-4) {
             k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_ut, u, c->d_du, n, 1.0, mu, nullptr);
             c->launches++;
-            if ((rc = residual_launch(c, c->d_ut, c->d_Ft, BFS_FP64, s))) return finish(rc);
+            if ((rc = residual_launch(c, c->d_ut, c->d_Ft, c->opt.outer_precision, s))) return finish(rc);
             S.residual_evals_fp64++;
             norms_launch(c, c->d_Ft, n, c->d_scal + 12, c->d_scal + 13, s);
             if ((rc = read_scalars(c, c->d_scal + 12, 2, s))) return finish(rc);

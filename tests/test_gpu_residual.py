@@ -60,16 +60,19 @@ def _guesses(mesh):
             "perturbed": W.perturbed_guess(mesh, 2, 1e-2)}
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("name", list(MESHES))
-def test_residual_fp64_matches_oracle(name):
+def test_residual_fp64_matches_oracle(name, prec):
+    """FP64 and double-float residuals both meet the FP64 bar."""
     from paper_1709_08803_gb300 import bfs
     mesh, F = MESHES[name]
     topo = _topo(mesh)
     ctx = _ctx(mesh, topo, F)
     P = O.problem(mesh, F)
+    pr = bfs.BFS_FP64 if prec == "fp64" else bfs.BFS_DF64
     for gname, u in _guesses(mesh).items():
         ref, sc = O.residual(P, topo, u, with_scale=True)
-        got = ctx.residual(_dev(u), precision=bfs.BFS_FP64).cpu().numpy()
+        got = ctx.residual(_dev(u), precision=pr).cpu().numpy()
         err = np.abs(got - ref)
         assert np.all(err <= TOL64 * sc + 1e-13), (name, gname, float((err / (sc + 1e-300)).max()))
         assert ctx.check_finite()
@@ -156,7 +159,7 @@ def test_nan_input_is_flagged():
     assert st["status"] == bfs.BFS_ENAN
 
 
-@pytest.mark.parametrize("kprec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("kprec", ["fp64", "fp32c", "fp32c+df64"])
 def test_solve_small_config_matches_oracle(kprec):
     from paper_1709_08803_gb300 import bfs
     mesh, topo, F = W.config_small_half()
@@ -164,7 +167,9 @@ def test_solve_small_config_matches_oracle(kprec):
     uref, sref = O.jfnk(P, topo, W.flat_guess(mesh), tol=1e-11)
     assert sref["status"] == 0
     prec = bfs.BFS_FP64 if kprec == "fp64" else bfs.BFS_FP32C
-    ctx = _ctx(mesh, topo, F, tol=1e-11, krylov_precision=prec, eta=1e-4 if kprec == "fp64" else 1e-2)
+    outer = bfs.BFS_DF64 if kprec.endswith("df64") else bfs.BFS_FP64
+    ctx = _ctx(mesh, topo, F, tol=1e-11, krylov_precision=prec, outer_precision=outer,
+               eta=1e-4 if kprec == "fp64" else 1e-2)
     u = ctx.flat_guess()
     st = ctx.solve(u)
     print(f"solve {kprec}: {st}")
@@ -205,12 +210,15 @@ def paper_scale():
     return mesh, topo, F, P, u, ref, sc
 
 
-def test_paper_scale_residual_fp64(paper_scale):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_paper_scale_residual_fp64(paper_scale, prec):
     from paper_1709_08803_gb300 import bfs
     mesh, topo, F, P, u, ref, sc = paper_scale
     ctx = _ctx(mesh, topo, F)
-    got = ctx.residual(_dev(u), precision=bfs.BFS_FP64).cpu().numpy()
+    pr = bfs.BFS_FP64 if prec == "fp64" else bfs.BFS_DF64
+    got = ctx.residual(_dev(u), precision=pr).cpu().numpy()
     rel = np.abs(got - ref) / (sc + 1e-300)
+    print(f"{prec} 181x61: max |dF|/scale = {rel.max():.3e}")
     assert rel.max() <= TOL64, rel.max()
 
 
@@ -232,10 +240,11 @@ def test_paper_scale_mixed_solve_is_a_root(F):
     from paper_1709_08803_gb300 import bfs
     mesh, topo, _ = W.config_paper_scale(F)
     P = O.problem(mesh, F)
-    ctx = _ctx(mesh, topo, F, tol=1e-8, krylov_precision=bfs.BFS_FP32C, eta=1e-2)
+    ctx = _ctx(mesh, topo, F, tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
+               eta=1e-2)
     u = ctx.flat_guess()
     st = ctx.solve(u)
-    print(f"181x61 F={F} mixed: {st}")
+    print(f"181x61 F={F} mixed (FP32C Krylov, DF64 Newton): {st}")
     ug = u.cpu().numpy()
     assert np.abs(O.residual(P, topo, ug)).max() <= 1.5e-8
     ctx64 = _ctx(mesh, topo, F, tol=1e-8)
