@@ -123,6 +123,19 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
               bfs_ctx **out);
 
 void bfs_destroy(bfs_ctx *ctx);
+
+/* Replace the topography of a context (HOST arrays as in bfs_setup) and
+   recompute its bottom-only integral part; the factored preconditioner stays
+   valid because the linearised Jacobian does not depend on the bottom
+   (Sec. 4.2).  This is the continuation step in bump height that the
+   paper's large-amplitude solutions rely on (Sec. 5).  Synchronous; errors as
+   bfs_setup's topography checks. */
+int bfs_set_topography(bfs_ctx *ctx, const bfs_topo *topo);
+
+/* Change the Froude number.  The factored preconditioner (formed for the
+   previous F) is kept as an approximation and stays usable; call
+   bfs_precond_factor to refresh it.  BFS_EINVAL for F <= 0. */
+int bfs_set_froude(bfs_ctx *ctx, double F);
 const char *bfs_last_error(const bfs_ctx *ctx);
 int bfs_n_unknowns(const bfs_ctx *ctx);
 /* Pair evaluations of one residual: 4 (N-1)M x (number of sources). */
@@ -183,13 +196,51 @@ int bfs_flat_guess(bfs_ctx *ctx, double *u, void *stream);
 int bfs_unpack(bfs_ctx *ctx, const double *u, double *out, void *stream);
 
 /* Profiling.  bfs_profile_enable(ctx, 1) records a CUDA event pair on the
-   launching stream around every pair-kernel launch of the context;
-   bfs_profile_read waits for the recorded events and returns, in out6,
-   {total ms and launch count} of the FP64, FP32C and DF64 pair kernels in
-   that order, then forgets them.  *launches (optional)
+   launching stream around every pair-kernel launch and every preconditioner
+   apply of the context; bfs_profile_read waits for the recorded events and
+   returns, in out8, {total ms and launch count} of the FP64, FP32C and DF64
+   pair kernels and of the preconditioner apply, in that order, then forgets
+   them.  *launches (optional)
    receives the number of kernels the context has launched since bfs_setup. */
 int bfs_profile_enable(bfs_ctx *ctx, int on);
-int bfs_profile_read(bfs_ctx *ctx, double *out6, unsigned long long *launches);
+int bfs_profile_read(bfs_ctx *ctx, double *out8, unsigned long long *launches);
+
+/* Batched sweeps (spec extension; the paper solves one problem at a
+   time).  A batch holds B independent problems -- each its own mesh, bottom
+   and Froude number -- and evaluates the FP32C residuals that their Krylov
+   iterations need in ONE persistent-kernel launch per step: CTAs take
+   (instance, target tile, source split) items from a queue, largest
+   instances first, so uneven meshes share the GPU evenly.  That batched
+   residual is captured once as a CUDA graph and replayed.
+     bfs_batch_setup: B problems (arrays of B meshes, topographies and F; the
+       same options for all).  Each instance owns a context; errors as
+       bfs_setup, prefixed with the instance index (bfs_batch_last_error(NULL)).
+     bfs_batch_residual: Fu[i] = F(u[i]) in FP32C for every instance; u, Fu:
+       HOST arrays of B DEVICE pointers.  Asynchronous.
+     bfs_batch_autotune: times the persistent kernel's tile shapes on the batch
+       and keeps the fastest (*ms_out: its batched-residual time).  Synchronous.
+     bfs_batch_tuning: the chosen shape and the time of every candidate
+       (ms_per_variant: 8 entries, -1 where not run).
+     bfs_batch_solve: bfs_solve for every instance, in lockstep (u: host array of
+       B device pointers; st: B stats or NULL).  Factors preconditioners that
+       are not yet factored.  Synchronous.  Returns BFS_OK when every instance
+       converged, otherwise the status of a failing instance (each instance's
+       own status is in st[i].status).
+     bfs_batch_instance: the context of instance i (owned by the batch), for
+       the single-instance calls. */
+typedef struct bfs_batch bfs_batch;
+int bfs_batch_setup(int B, const bfs_mesh *meshes, const bfs_topo *topos, const double *F,
+                    const bfs_options *opt, bfs_batch **out);
+void bfs_batch_destroy(bfs_batch *b);
+const char *bfs_batch_last_error(const bfs_batch *b);
+int bfs_batch_size(const bfs_batch *b);
+int bfs_batch_n_unknowns(const bfs_batch *b, int i);
+double bfs_batch_pair_evals(const bfs_batch *b);
+bfs_ctx *bfs_batch_instance(bfs_batch *b, int i);
+int bfs_batch_residual(bfs_batch *b, const double *const *u, double *const *Fu, void *stream);
+int bfs_batch_autotune(bfs_batch *b, void *stream, double *ms_out);
+int bfs_batch_tuning(const bfs_batch *b, int *variant, int *tpb, int *tpt, double *ms_per_variant);
+int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream);
 
 /* Residual for callers that cannot allocate device memory.  The paper has no
    counterpart: this is a library convenience.  Code that runs where a device

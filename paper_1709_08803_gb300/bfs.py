@@ -100,6 +100,24 @@ def lib():
                                           ctypes.c_double, _VP, _VP, ctypes.c_int, _VP]
         L.bfs_static_last_error.restype = ctypes.c_char_p
         L.bfs_static_scratch_bytes.restype = ctypes.c_size_t
+        L.bfs_batch_setup.argtypes = [ctypes.c_int, C(bfs_mesh), C(bfs_topo), C(ctypes.c_double),
+                                      C(bfs_options), C(_VP)]
+        L.bfs_batch_destroy.argtypes = [_VP]
+        L.bfs_batch_last_error.argtypes = [_VP]
+        L.bfs_batch_last_error.restype = ctypes.c_char_p
+        L.bfs_batch_size.argtypes = [_VP]
+        L.bfs_batch_n_unknowns.argtypes = [_VP, ctypes.c_int]
+        L.bfs_batch_pair_evals.argtypes = [_VP]
+        L.bfs_batch_pair_evals.restype = ctypes.c_double
+        L.bfs_batch_instance.argtypes = [_VP, ctypes.c_int]
+        L.bfs_batch_instance.restype = _VP
+        L.bfs_batch_residual.argtypes = [_VP, C(_VP), C(_VP), _VP]
+        L.bfs_batch_autotune.argtypes = [_VP, _VP, C(ctypes.c_double)]
+        L.bfs_batch_tuning.argtypes = [_VP, C(ctypes.c_int), C(ctypes.c_int), C(ctypes.c_int),
+                                       C(ctypes.c_double)]
+        L.bfs_batch_solve.argtypes = [_VP, C(_VP), C(bfs_stats), _VP]
+        L.bfs_set_topography.argtypes = [_VP, C(bfs_topo)]
+        L.bfs_set_froude.argtypes = [_VP, ctypes.c_double]
         L.bfs_profile_enable.argtypes = [_VP, ctypes.c_int]
         L.bfs_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_ulonglong)]
@@ -236,17 +254,26 @@ class Context:
         self._check(lib().bfs_flat_guess(self._ctx, self._vec(out), _stream(stream)))
         return out
 
+    def set_topography(self, topo):
+        self._h = [np.ascontiguousarray(a, dtype=np.float64) for a in (topo.beta, topo.beta_x, topo.beta_y)]
+        D = ctypes.POINTER(ctypes.c_double)
+        t = bfs_topo(*[a.ctypes.data_as(D) for a in self._h])
+        self._check(lib().bfs_set_topography(self._ctx, ctypes.byref(t)))
+
+    def set_froude(self, F: float):
+        self._check(lib().bfs_set_froude(self._ctx, float(F)))
+
     def profile_enable(self, on: bool = True):
         self._check(lib().bfs_profile_enable(self._ctx, int(bool(on))))
 
     def profile_read(self):
         """Returns {"fp64"|"fp32c"|"df64": (total ms, launches)} of the pair kernels
         since the last read, and the context's kernel-launch counter."""
-        out = (ctypes.c_double * 6)()
+        out = (ctypes.c_double * 8)()
         n = ctypes.c_ulonglong()
         self._check(lib().bfs_profile_read(self._ctx, out, ctypes.byref(n)))
         return ({"fp64": (out[0], int(out[1])), "fp32c": (out[2], int(out[3])),
-                 "df64": (out[4], int(out[5]))}, int(n.value))
+                 "df64": (out[4], int(out[5])), "apply": (out[6], int(out[7]))}, int(n.value))
 
     def unpack(self, u, stream=None):
         import torch
@@ -274,3 +301,99 @@ def residual_static(mesh, beta, beta_x, beta_y, F: float, u, out=None, precision
     if rc != BFS_OK:
         raise BfsError(rc, lib().bfs_static_last_error().decode())
     return out
+
+
+class Batch:
+    """Many independent problems solved together (wraps bfs_batch)."""
+
+    def __init__(self, meshes, topos, Fs, options: bfs_options | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA device required: libbfs has no CPU path")
+        B = len(meshes)
+        assert len(topos) == B and len(Fs) == B
+        self.meshes = list(meshes)
+        D = ctypes.POINTER(ctypes.c_double)
+        self._h = []
+        ms = (bfs_mesh * B)()
+        ts = (bfs_topo * B)()
+        for i, (m, t) in enumerate(zip(meshes, topos)):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (t.beta, t.beta_x, t.beta_y)]
+            self._h.append(arrs)
+            ms[i] = bfs_mesh(m.N, m.M, int(m.half), m.x1, m.y1, m.dx, m.dy)
+            ts[i] = bfs_topo(*[a.ctypes.data_as(D) for a in arrs])
+        F = (ctypes.c_double * B)(*[float(f) for f in Fs])
+        self.options = options if options is not None else default_options()
+        h = _VP()
+        rc = lib().bfs_batch_setup(B, ms, ts, F, ctypes.byref(self.options), ctypes.byref(h))
+        if rc != BFS_OK:
+            raise BfsError(rc, lib().bfs_batch_last_error(None).decode())
+        self._b = h
+        self.B = B
+        self.n = [lib().bfs_batch_n_unknowns(h, i) for i in range(B)]
+        self.pair_evals = lib().bfs_batch_pair_evals(h)
+
+    def _check(self, rc):
+        if rc != BFS_OK:
+            raise BfsError(rc, lib().bfs_batch_last_error(self._b).decode())
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().bfs_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, ts):
+        import torch
+        assert len(ts) == self.B
+        for t, n in zip(ts, self.n):
+            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n
+        return (_VP * self.B)(*[_ptr(t) for t in ts])
+
+    def flat_guesses(self):
+        import torch
+        out = []
+        for i in range(self.B):
+            u = torch.empty(self.n[i], dtype=torch.float64, device="cuda")
+            rc = lib().bfs_flat_guess(lib().bfs_batch_instance(self._b, i), ctypes.c_void_p(_ptr(u)),
+                                      _stream(None))
+            self._check(rc)
+            out.append(u)
+        return out
+
+    def residual(self, us, outs=None, stream=None):
+        import torch
+        if outs is None:
+            outs = [torch.empty_like(u) for u in us]
+        self._check(lib().bfs_batch_residual(self._b, self._ptrs(us), self._ptrs(outs), _stream(stream)))
+        return outs
+
+    def instance_residual(self, i, u, precision: int = BFS_FP64, stream=None):
+        import torch
+        out = torch.empty_like(u)
+        self._check(lib().bfs_residual(lib().bfs_batch_instance(self._b, i), ctypes.c_void_p(_ptr(u)),
+                                       ctypes.c_void_p(_ptr(out)), precision, _stream(stream)))
+        return out
+
+    def autotune(self, stream=None) -> float:
+        ms = ctypes.c_double()
+        self._check(lib().bfs_batch_autotune(self._b, _stream(stream), ctypes.byref(ms)))
+        return ms.value
+
+    def tuning(self) -> dict:
+        v, tpb, tpt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 8)()
+        self._check(lib().bfs_batch_tuning(self._b, ctypes.byref(v), ctypes.byref(tpb), ctypes.byref(tpt), ms))
+        return {"variant": v.value, "tpb": tpb.value, "tpt": tpt.value, "ms_per_variant": list(ms)[:5]}
+
+    def solve(self, us, stream=None, raise_on_error: bool = False):
+        st = (bfs_stats * self.B)()
+        rc = lib().bfs_batch_solve(self._b, self._ptrs(us), st, _stream(stream))
+        if raise_on_error:
+            self._check(rc)
+        return rc, [x.as_dict() for x in st]

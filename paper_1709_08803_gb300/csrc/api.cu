@@ -187,6 +187,37 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     return BFS_OK;
 }
 
+int bfs_set_topography(bfs_ctx *c, const bfs_topo *topo)
+{
+    if (!c || !topo || !topo->beta || !topo->beta_x || !topo->beta_y)
+        return set_err(c, BFS_EINVAL, "NULL argument");
+    const size_t NM = (size_t)c->NM;
+    for (size_t q = 0; q < NM; q++) {
+        if (!isfinite(topo->beta[q]) || !isfinite(topo->beta_x[q]) || !isfinite(topo->beta_y[q]))
+            return set_err(c, BFS_EINVAL, "topography has a non-finite value");
+        if (!(topo->beta[q] < 0.0))
+            return set_err(c, BFS_EINVAL, "the bottom must stay below z = 0 (beta < 0)");
+    }
+    BFS_CUDA_TRY(c, cudaDeviceSynchronize());
+    BFS_CUDA_TRY(c, cudaMemcpy(c->d_beta, topo->beta, sizeof(double) * NM, cudaMemcpyHostToDevice));
+    BFS_CUDA_TRY(c, cudaMemcpy(c->d_bx, topo->beta_x, sizeof(double) * NM, cudaMemcpyHostToDevice));
+    BFS_CUDA_TRY(c, cudaMemcpy(c->d_by, topo->beta_y, sizeof(double) * NM, cudaMemcpyHostToDevice));
+    double *u0 = c->d_Fp;
+    k_flat_guess<<<(c->n + 255) / 256, 256>>>(u0, c->N, c->M, c->x1);
+    c->launches++;
+    if (bfs::unpack_launch(c, u0, 0) || bfs::constB_launch(c, 0)) return BFS_ECUDA;
+    BFS_CUDA_TRY(c, cudaDeviceSynchronize());
+    return BFS_OK;
+}
+
+int bfs_set_froude(bfs_ctx *c, double F)
+{
+    if (!c) return BFS_EINVAL;
+    if (!(F > 0.0) || !isfinite(F)) return set_err(c, BFS_EINVAL, "F must be positive");
+    c->F = F;
+    return BFS_OK;
+}
+
 void bfs_destroy(bfs_ctx *c)
 {
     if (!c) return;
@@ -316,19 +347,19 @@ int bfs_profile_enable(bfs_ctx *c, int on)
     return BFS_OK;
 }
 
-int bfs_profile_read(bfs_ctx *c, double *out6, unsigned long long *launches)
+int bfs_profile_read(bfs_ctx *c, double *out8, unsigned long long *launches)
 {
     if (!c) return BFS_EINVAL;
     if (launches) *launches = c->launches;
-    if (!out6) return BFS_OK;
-    for (int i = 0; i < 6; i++) out6[i] = 0.0;
+    if (!out8) return BFS_OK;
+    for (int i = 0; i < 8; i++) out8[i] = 0.0;
     for (size_t i = 0; i < c->ev_kind.size(); i++) {
         float ms = 0.0f;
         BFS_CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[2 * i + 1]));
         BFS_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
         int k = c->ev_kind[i];
-        out6[2 * k] += ms;
-        out6[2 * k + 1] += 1.0;
+        out8[2 * k] += ms;
+        out8[2 * k + 1] += 1.0;
     }
     c->ev_used = 0;
     c->ev_kind.clear();

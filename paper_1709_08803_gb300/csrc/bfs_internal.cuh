@@ -37,6 +37,18 @@ constexpr int TREC = 16;
 //   4  single layer of the top sheet at bottom targets
 constexpr int NACC = 5;
 
+// One instance of a batched sweep as the persistent pair kernel sees it.
+struct BatchInst {
+    const float *src;
+    const float *tgt;
+    double *part;
+    int Nt, per_split;
+};
+
+struct BatchVariant {
+    int tpb, tpt;
+};
+
 struct PairPlan {
     int tpb;        // threads per CTA
     int tpt;        // targets per thread
@@ -113,11 +125,39 @@ int constB_launch(bfs_ctx *c, cudaStream_t s);
 PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, int sms);
 void plans_for(int Nt, int Ns, int splits_req, int sms, PairPlan *p64, PairPlan *p32);
 
+int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s);
+extern const BatchVariant kBatchVariants[];
+extern const int kNumBatchVariants;
+int batch_pairs_occupancy(int v, int *blocks_per_sm);
+void batch_pairs_launch(int v, int grid, const BatchInst *inst, const int4 *items, int n_items,
+                        unsigned int *counter, const unsigned char *mask, cudaStream_t s);
+
 // pairs_df64.cu
 PairPlan plan_df(int Nt, int Ns, int splits_req, int sms);
 int pairs_df_launch(bfs_ctx *c, cudaStream_t s);
 
 // solver.cu
+// GMRES state of one instance between device phases (see solver.cu).
+struct Gm {
+    enum State { BEGIN, ARNOLDI, CYCLE_END, RESTART, DONE };
+    const double *u, *F, *Fbase;
+    double target, res;
+    int maxit, its, j, status, precs, jvs;
+    State state;
+};
+void gm_start(bfs_ctx *c, Gm &g, const double *u, const double *F, const double *Fbase,
+              double fnorm2, double eta, int maxit, cudaStream_t s);
+void gm_cycle_begin(bfs_ctx *c, Gm &g, double beta, cudaStream_t s);
+int gm_arnoldi_pre(bfs_ctx *c, Gm &g, cudaStream_t s);
+int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s);
+void gm_arnoldi_host(bfs_ctx *c, Gm &g, double hn, double res);
+int gm_cycle_end(bfs_ctx *c, Gm &g, cudaStream_t s);
+int gm_restart_post(bfs_ctx *c, Gm &g, cudaStream_t s);
+int jv_prep(bfs_ctx *c, const double *u, const double *z, double h, int precision, cudaStream_t s,
+            bool unorm_ready);
+int jv_post(bfs_ctx *c, const double *Fu, double *Jz, cudaStream_t s);
+void solver_axpby(bfs_ctx *c, double *y, const double *x, const double *z, double a, double b,
+                  cudaStream_t s);
 int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
                double h, int precision, cudaStream_t s, bool unorm_ready = false);
 int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s);

@@ -350,6 +350,7 @@ struct CoopBar {
     unsigned int gen;
 };
 
+// Barrier of the Gauss-Jordan kernel (one per pivot column).
 __device__ bool grid_sync(CoopBar *b, int *flag)
 {
     __shared__ int ok;
@@ -372,10 +373,40 @@ __device__ bool grid_sync(CoopBar *b, int *flag)
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
+    }
+    __syncthreads();
+    return ok;
+}
+
+// Barrier of the apply kernel: the counter only grows within a launch (it is
+// zeroed before each launch); barrier number e completes when the counter
+// reaches e * gridDim.x.  Arrival is a release add, the wait an acquire load,
+// so no separate fences are needed.  The wait is bounded (about a second);
+// on timeout bit 2 of the flag is raised and false is returned.
+__device__ __forceinline__ bool grid_sync_epoch(unsigned int *count, unsigned int epoch, int *flag)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        unsigned int old;
+        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        const unsigned int target = epoch * gridDim.x;
+        unsigned int v = old + 1, spins = 0;
+        while (v < target) {
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            if (++spins > (1u << 24)) {
+                atomicOr(flag, 2);
+                ok = 0;
+                break;
+            }
+            __nanosleep(16);
+        }
     }
     __syncthreads();
     return ok;
@@ -390,83 +421,98 @@ struct ApplyArgs {
     int *flag;
 };
 
-constexpr int AP_TPB = 256;
+constexpr int AP_TPB = 1024;
+constexpr int AP_WARPS = AP_TPB / 32;
 
-// sum over blocks b of sgn_b * (row `row` of block b) . vec_b, split over the
-// 8 warps of the CTA by column ranges; returned to thread 0
-template <int MAXB>
-__device__ __forceinline__ double row_dots(const double *const *blk, const double *const *vec,
-                                           const double *sgn, int cnt, int row, int nb, double *red)
+// One CTA per SM.  Rows of a slice are dealt out round-robin over the CTAs,
+// and within a CTA over groups of warps; the warps of a group split the
+// columns of every block of the row and add their partial dots in shared
+// memory.
+__global__ void __launch_bounds__(AP_TPB, 1) k_apply_coop(ApplyArgs a)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cw = (nb + (AP_TPB / 32) - 1) / (AP_TPB / 32);
-    const int c0 = warp * cw, c1 = min(nb, c0 + cw);
-    double acc = 0.0;
-    for (int b = 0; b < cnt; b++) {
-        const double *rp = blk[b] + (size_t)row * nb;
-        const double *v = vec[b];
-        double t = 0.0;
-        for (int c = c0 + lane; c < c1; c += 32) t = fma(__ldg(rp + c), __ldcg(v + c), t);
-        acc = fma(sgn[b], t, acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < AP_TPB / 32; w++) s += red[w];
-    __syncthreads();
-    return s;
-}
-
-__global__ void __launch_bounds__(AP_TPB) k_apply_coop(ApplyArgs a)
-{
-    __shared__ double red[AP_TPB / 32];
+    __shared__ double red[AP_WARPS];
     const int nb = a.nb, NB = a.NB, M = a.M, h = a.h, nd = 2 * h + 1;
     const size_t bsz = (size_t)nb * nb;
     const int n = 3 * NB * M;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rpc = (nb + gridDim.x - 1) / gridDim.x;          // rows per CTA
+    const int groups = min(rpc, AP_WARPS);                      // warp groups
+    const int wpg = AP_WARPS / groups;                          // warps per group
+    const int grp = warp / wpg, wig = warp - grp * wpg;
+    const int cw = (nb + wpg - 1) / wpg;
+    const int c0 = wig * cw, c1 = min(nb, c0 + cw);
+    unsigned int *cnt = &a.bar->count;
+    unsigned int epoch = 0;
+    // rows of block row k that this warp reads, for the prefetch of the next step
+    auto prefetch_step = [&](int pass, int k) {
+        if (k < 0 || k >= M) return;
+        int lo2, hi2;
+        if (pass == 0) { lo2 = max(0, k - h); hi2 = k - 1; }
+        else { lo2 = k; hi2 = min(M - 1, k + h); }
+        for (int rb = 0; rb < rpc; rb += groups) {
+            const int rr = rb + grp;
+            if (grp >= groups || rr >= rpc) continue;
+            const int row = blockIdx.x + rr * gridDim.x;
+            if (row >= nb) continue;
+            for (int m = lo2; m <= hi2; m++) {
+                const double *rp = a.pc + ((size_t)k * nd + (m - k + h)) * bsz + (size_t)row * nb;
+                for (int c = c0 + lane * 16; c < c1; c += 32 * 16)  // one 128-byte line per 16 doubles
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + c));
+            }
+        }
+    };
+    prefetch_step(0, 0);
+    prefetch_step(0, 1);
     for (int e = gtid; e < n; e += gstride) {
         int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
         __stcg(a.x + (size_t)l * nb + g * NB + p, a.r[e]);
     }
-    if (!grid_sync(a.bar, a.flag)) return;
-    const double *blk[17];
-    const double *vec[17];
-    double sgn[17];
-    // forward: y_k = x_k - sum_{i<k} L_ki y_i
-    for (int k = 0; k < M; k++) {
-        int cnt = 0;
-        for (int i = max(0, k - h); i < k; i++) {
-            blk[cnt] = a.pc + ((size_t)k * nd + (i - k + h)) * bsz;
-            vec[cnt] = a.y + (size_t)i * nb;
-            sgn[cnt] = -1.0;
-            cnt++;
+    if (!grid_sync_epoch(cnt, ++epoch, a.flag)) return;
+    for (int pass = 0; pass < 2; pass++) {
+        for (int kk = 0; kk < M; kk++) {
+            const int k = pass == 0 ? kk : M - 1 - kk;
+            // the factor rows two steps ahead do not depend on this step: start
+            // bringing them into L2 now
+            {
+                const int k2 = pass == 0 ? k + 2 : k - 2;
+                if (k2 >= 0 && k2 < M) prefetch_step(pass, k2);
+                else if (pass == 0) prefetch_step(1, M - 1 - (k2 - M));
+            }
+            // blocks of this block row that enter the sweep
+            int lo, hi;
+            if (pass == 0) { lo = max(0, k - h); hi = k - 1; }   // L_ki, i < k, against y_i
+            else { lo = k; hi = min(M - 1, k + h); }             // D_k^-1 y_k, W_kj x_j
+            // the trip count is the same for every thread of the CTA (the
+            // loop body has barriers); threads without a row compute nothing
+            for (int rb = 0; rb < rpc; rb += groups) {
+                const int rr = rb + grp;
+                const int row = (grp < groups && rr < rpc) ? blockIdx.x + rr * gridDim.x : nb;
+                double acc = 0.0;
+                if (row < nb) {
+                    for (int m = lo; m <= hi; m++) {
+                        const double *rp = a.pc + ((size_t)k * nd + (m - k + h)) * bsz + (size_t)row * nb;
+                        const double *v = (pass == 0 || m == k) ? a.y + (size_t)m * nb : a.x + (size_t)m * nb;
+                        const double sg = (pass == 1 && m == k) ? 1.0 : -1.0;
+                        double t = 0.0;
+#pragma unroll 4
+                        for (int c = c0 + lane; c < c1; c += 32) t = fma(__ldg(rp + c), __ldcg(v + c), t);
+                        acc = fma(sg, t, acc);
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+                if (lane == 0) red[warp] = acc;
+                __syncthreads();
+                if (wig == 0 && lane == 0 && row < nb) {
+                    double s = 0.0;
+                    for (int w = 0; w < wpg; w++) s += red[grp * wpg + w];  // grp < groups here
+                    if (pass == 0) __stcg(a.y + (size_t)k * nb + row, __ldcg(a.x + (size_t)k * nb + row) + s);
+                    else __stcg(a.x + (size_t)k * nb + row, s);
+                }
+                __syncthreads();
+            }
+            if (!grid_sync_epoch(cnt, ++epoch, a.flag)) return;
         }
-        for (int row = blockIdx.x; row < nb; row += gridDim.x) {
-            double s = row_dots<17>(blk, vec, sgn, cnt, row, nb, red);
-            if (threadIdx.x == 0) __stcg(a.y + (size_t)k * nb + row, __ldcg(a.x + (size_t)k * nb + row) + s);
-        }
-        if (!grid_sync(a.bar, a.flag)) return;
-    }
-    // backward: x_k = D_k^-1 y_k - sum_{j>k} W_kj x_j
-    for (int k = M - 1; k >= 0; k--) {
-        int cnt = 0;
-        blk[cnt] = a.pc + ((size_t)k * nd + h) * bsz;
-        vec[cnt] = a.y + (size_t)k * nb;
-        sgn[cnt] = 1.0;
-        cnt++;
-        for (int j = k + 1; j <= min(M - 1, k + h); j++) {
-            blk[cnt] = a.pc + ((size_t)k * nd + (j - k + h)) * bsz;
-            vec[cnt] = a.x + (size_t)j * nb;
-            sgn[cnt] = -1.0;
-            cnt++;
-        }
-        for (int row = blockIdx.x; row < nb; row += gridDim.x) {
-            double s = row_dots<17>(blk, vec, sgn, cnt, row, nb, red);
-            if (threadIdx.x == 0) __stcg(a.x + (size_t)k * nb + row, s);
-        }
-        if (!grid_sync(a.bar, a.flag)) return;
     }
     for (int e = gtid; e < n; e += gstride) {
         int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
@@ -607,7 +653,7 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
             c->err = "apply kernel cannot be resident";
             return BFS_ECUDA;
         }
-        c->apply_grid = num_sms(c->device) * std::min(per_sm, 4);
+        c->apply_grid = num_sms(c->device);  // one 1024-thread CTA per SM
     }
     ApplyArgs a;
     a.pc = c->d_pc; a.r = r; a.z = z; a.x = c->d_perm_a; a.y = c->d_perm_b;
@@ -615,10 +661,18 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
     a.bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
     a.flag = c->d_flag;
     BFS_CUDA_TRY(c, cudaMemsetAsync(a.bar, 0, sizeof(CoopBar), s));
+    cudaEvent_t ev1 = nullptr;
+    if (c->prof_on) {
+        cudaEvent_t ev0 = prof_event(c);
+        ev1 = prof_event(c);
+        c->ev_kind.push_back(3);
+        cudaEventRecord(ev0, s);
+    }
     void *args[] = {&a};
     BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_apply_coop, dim3(c->apply_grid),
                                                 dim3(AP_TPB), args, 0, s));
     c->launches++;
+    if (ev1) cudaEventRecord(ev1, s);
     return BFS_OK;
 }
 

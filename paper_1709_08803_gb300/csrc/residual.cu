@@ -529,6 +529,70 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
     return BFS_OK;
 }
 
+int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s)
+{
+    const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
+    FinArgs fa = fin_args(c, p.splits);
+    int tot = 4 * (c->Nt + c->M);
+    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, Fu,
+                                               c->d_flag, fa);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// Persistent multi-instance FP32C pair kernel: CTAs take (instance, target
+// tile, source split) items from a queue until it is empty; items of masked
+// instances are skipped.
+template <int TPB, int TPT>
+__global__ void __launch_bounds__(TPB)
+k_pairs_batch(const BatchInst *__restrict__ inst, const int4 *__restrict__ items, int n_items,
+              unsigned int *__restrict__ counter, const unsigned char *__restrict__ mask)
+{
+    __shared__ __align__(16) float sh[P32_CH * REC];
+    __shared__ int it;
+    while (true) {
+        if (threadIdx.x == 0) it = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int w = it;
+        __syncthreads();
+        if (w >= n_items) return;
+        const int4 item = items[w];
+        if (!mask[item.x]) continue;
+        const BatchInst I = inst[item.x];
+        pair_tile<float, TPB, TPT, P32_CH, true>(I.src, I.per_split, I.tgt, I.Nt, I.part, item.y,
+                                                 item.z, sh);
+    }
+}
+
+const BatchVariant kBatchVariants[] = {{128, 2}, {256, 1}, {64, 2}, {128, 1}, {64, 4}};
+const int kNumBatchVariants = 5;
+
+int batch_pairs_occupancy(int v, int *blocks_per_sm)
+{
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (v) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pairs_batch<128, 2>, 128, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pairs_batch<256, 1>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pairs_batch<64, 2>, 64, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pairs_batch<128, 1>, 128, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pairs_batch<64, 4>, 64, 0); break;
+    }
+    return e == cudaSuccess ? 0 : -1;
+}
+
+void batch_pairs_launch(int v, int grid, const BatchInst *inst, const int4 *items, int n_items,
+                        unsigned int *counter, const unsigned char *mask, cudaStream_t s)
+{
+    switch (v) {
+    case 0: k_pairs_batch<128, 2><<<grid, 128, 0, s>>>(inst, items, n_items, counter, mask); break;
+    case 1: k_pairs_batch<256, 1><<<grid, 256, 0, s>>>(inst, items, n_items, counter, mask); break;
+    case 2: k_pairs_batch<64, 2><<<grid, 64, 0, s>>>(inst, items, n_items, counter, mask); break;
+    case 3: k_pairs_batch<128, 1><<<grid, 128, 0, s>>>(inst, items, n_items, counter, mask); break;
+    case 4: k_pairs_batch<64, 4><<<grid, 64, 0, s>>>(inst, items, n_items, counter, mask); break;
+    }
+}
+
 int constB_launch(bfs_ctx *c, cudaStream_t s)
 {
     FinArgs fa = fin_args(c, 1);

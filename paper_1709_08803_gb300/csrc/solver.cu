@@ -149,8 +149,17 @@ __global__ void k_jv_diff(double *__restrict__ Jz, const double *__restrict__ Fp
 
 static int grid_for(int n) { return (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184; }
 
-int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
-               double h, int precision, cudaStream_t s, bool unorm_ready)
+void solver_axpby(bfs_ctx *c, double *y, const double *x, const double *z, double a, double b,
+                  cudaStream_t s)
+{
+    k_axpby<<<grid_for(c->n), 256, 0, s>>>(y, x, z, c->n, a, b, nullptr);
+    c->launches++;
+}
+
+// First half of a Jacobian-vector product: h from |u| and |z| on the device,
+// u + h z into the context's perturbed-point buffer d_up.
+int jv_prep(bfs_ctx *c, const double *u, const double *z, double h, int precision, cudaStream_t s,
+            bool unorm_ready)
 {
     const int n = c->n;
     double h_rel = c->opt.jv_h_rel;
@@ -164,12 +173,26 @@ int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, d
     // u + h z (a zero z gives h = 0 and Jz = 0)
     k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_up, u, z, n, 1.0, 1.0, c->d_scal + 4);
     c->launches++;
-    int rc = residual_launch(c, c->d_up, c->d_Fp, precision, s);
-    if (rc) return rc;
-    k_jv_diff<<<grid_for(n), 256, 0, s>>>(Jz, c->d_Fp, Fu, n, c->d_scal);
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// Second half, after F(u + h z) is in d_Fp: Jz = (F(u + h z) - Fu) / h.
+int jv_post(bfs_ctx *c, const double *Fu, double *Jz, cudaStream_t s)
+{
+    k_jv_diff<<<grid_for(c->n), 256, 0, s>>>(Jz, c->d_Fp, Fu, c->n, c->d_scal);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());
     return BFS_OK;
+}
+
+int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
+               double h, int precision, cudaStream_t s, bool unorm_ready)
+{
+    int rc = jv_prep(c, u, z, h, precision, s, unorm_ready);
+    if (!rc) rc = residual_launch(c, c->d_up, c->d_Fp, precision, s);
+    if (!rc) rc = jv_post(c, Fu, Jz, s);
+    return rc;
 }
 
 // w -= V[0..cnt) h   (h on the device)
@@ -296,69 +319,139 @@ static void arnoldi_orth(bfs_ctx *c, int cnt, cudaStream_t s)
     norms_launch(c, c->d_w, n, c->d_scal + 8, nullptr, s);
 }
 
-// GMRES for J P^-1 y = -F at u; du = P^-1 V y.  Returns status; *its gets iterations.
-static int gmres(bfs_ctx *c, const double *u, const double *F, const double *Fbase, double fnorm2,
-                 double eta, int maxit, int *its_out, int *precs, int *jvs, cudaStream_t s)
+// ---------------------------------------------------------------------------
+// GMRES as a sequence of device phases with host decisions between them.  A
+// single solve drives one instance; the batched solve drives many in lockstep
+// and evaluates their residuals together.  Device scalars: d_scal[8] = |w|
+// (or beta at a cycle start), d_scal[9] = |g_{j+1}|.
+// ---------------------------------------------------------------------------
+void gm_start(bfs_ctx *c, Gm &g, const double *u, const double *F, const double *Fbase,
+              double fnorm2, double eta, int maxit, cudaStream_t s)
+{
+    const int n = c->n;
+    g.u = u; g.F = F; g.Fbase = Fbase;
+    g.target = eta * fnorm2;
+    g.maxit = maxit;
+    g.its = 0; g.j = 0; g.res = 0.0; g.state = Gm::BEGIN; g.status = BFS_OK;
+    cudaMemsetAsync(c->d_du, 0, sizeof(double) * n, s);
+    norms_launch(c, u, n, c->d_scal + 0, nullptr, s);  // |u| is fixed during the solve
+    k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, F, n, -1.0, 0.0, nullptr);  // r = -F
+    c->launches++;
+    norms_launch(c, c->d_w, n, c->d_scal + 8, nullptr, s);
+}
+
+// With beta = |r| read: finish, or start a cycle (V_0 = r / beta, g = beta e_1).
+void gm_cycle_begin(bfs_ctx *c, Gm &g, double beta, cudaStream_t s)
 {
     const int m = c->m_alloc, n = c->n;
-    const size_t ldv = (size_t)n;
-    int its = 0, rc;
-    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_du, 0, sizeof(double) * n, s));
-    norms_launch(c, u, n, c->d_scal + 0, nullptr, s);  // |u| is fixed during the solve
-    // r = -F
-    k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, F, n, -1.0, 0.0, nullptr);
+    if (!isfinite(beta)) { g.status = BFS_ENAN; g.state = Gm::DONE; return; }
+    if (beta <= g.target || g.its >= g.maxit) { g.state = Gm::DONE; return; }
+    k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V, c->d_w, n, c->d_scal + 8);
     c->launches++;
-    const double target = eta * fnorm2;
-    int status = BFS_OK;
-    while (true) {
-        norms_launch(c, c->d_w, n, c->d_scal + 8, nullptr, s);
-        if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
-        double beta = c->h_pin[0];
-        if (!isfinite(beta)) return BFS_ENAN;
-        if (beta <= target || its >= maxit) break;
-        k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V, c->d_w, n, c->d_scal + 8);
-        c->launches++;
-        k_gmres_init<<<1, 1, 0, s>>>(c->d_giv, m, c->d_scal + 8);
-        c->launches++;
-        int j = 0;
-        double res = beta;
-        for (; j < m && its < maxit; j++) {
-            double *vj = c->d_V + (size_t)j * ldv;
-            if ((rc = precond_apply(c, vj, c->d_z, s))) return rc;
-            (*precs)++;
-            if ((rc = jvp_launch(c, u, Fbase, c->d_z, c->d_w, 0.0, c->opt.krylov_precision, s, true))) return rc;
-            (*jvs)++;
-            arnoldi_orth(c, j + 1, s);
-            k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V + (size_t)(j + 1) * ldv, c->d_w, n,
-                                                     c->d_scal + 8);
-            c->launches++;
-            k_givens<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, j, c->d_scal + 8, c->d_scal + 9);
-            c->launches++;
-            if ((rc = read_scalars(c, c->d_scal + 8, 2, s))) return rc;
-            its++;
-            res = c->h_pin[1];
-            if (!isfinite(res)) return BFS_ENAN;
-            if (res <= target) { j++; break; }
-            if (c->h_pin[0] == 0.0) { j++; break; }  // invariant subspace reached
-        }
-        // du += P^-1 V y
-        k_trisolve<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, j);
-        c->launches++;
-        k_gemv<<<grid_for(n), 256, 0, s>>>(c->d_w, c->d_V, ldv, c->d_giv + 3 * m + 1, j, n);
-        c->launches++;
-        if ((rc = precond_apply(c, c->d_w, c->d_z, s))) return rc;
-        (*precs)++;
-        k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_du, c->d_du, c->d_z, n, 1.0, 1.0, nullptr);
-        c->launches++;
-        if (res <= target || its >= maxit) break;
-        // restart: r = -F - J du
-        if ((rc = jvp_launch(c, u, Fbase, c->d_du, c->d_w, 0.0, c->opt.krylov_precision, s, true))) return rc;
-        (*jvs)++;
-        k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, c->d_w, n, -1.0, -1.0, nullptr);
-        c->launches++;
+    k_gmres_init<<<1, 1, 0, s>>>(c->d_giv, m, c->d_scal + 8);
+    c->launches++;
+    g.j = 0;
+    g.res = beta;
+    g.state = Gm::ARNOLDI;
+}
+
+// Arnoldi step, before the residual: z = P^-1 v_j, then u + h z into d_up.
+int gm_arnoldi_pre(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    int rc = precond_apply(c, c->d_V + (size_t)g.j * c->n, c->d_z, s);
+    if (rc) return rc;
+    g.precs++;
+    return jv_prep(c, g.u, c->d_z, 0.0, c->opt.krylov_precision, s, true);
+}
+
+// Arnoldi step, after F(u + h z) is in d_Fp: w = J z, CGS2, V_{j+1}, Givens.
+int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    const int m = c->m_alloc, n = c->n;
+    int rc = jv_post(c, g.Fbase, c->d_w, s);
+    if (rc) return rc;
+    g.jvs++;
+    arnoldi_orth(c, g.j + 1, s);
+    k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V + (size_t)(g.j + 1) * n, c->d_w, n, c->d_scal + 8);
+    c->launches++;
+    k_givens<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, g.j, c->d_scal + 8, c->d_scal + 9);
+    c->launches++;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// With (|w|, |g_{j+1}|) read: count the step; end the cycle on convergence,
+// an invariant subspace, a full basis or the iteration limit.
+void gm_arnoldi_host(bfs_ctx *c, Gm &g, double hn, double res)
+{
+    g.its++;
+    g.j++;
+    g.res = res;
+    if (!isfinite(res)) { g.status = BFS_ENAN; g.state = Gm::DONE; return; }
+    if (res <= g.target || hn == 0.0 || g.j >= c->m_alloc || g.its >= g.maxit) g.state = Gm::CYCLE_END;
+}
+
+// End of a cycle: du += P^-1 V y.  Then either done, or a restart needs
+// J du (prepared here: u + h du into d_up; the caller evaluates its residual).
+int gm_cycle_end(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    const int m = c->m_alloc, n = c->n;
+    k_trisolve<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, g.j);
+    c->launches++;
+    k_gemv<<<grid_for(n), 256, 0, s>>>(c->d_w, c->d_V, (size_t)n, c->d_giv + 3 * m + 1, g.j, n);
+    c->launches++;
+    int rc = precond_apply(c, c->d_w, c->d_z, s);
+    if (rc) return rc;
+    g.precs++;
+    k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_du, c->d_du, c->d_z, n, 1.0, 1.0, nullptr);
+    c->launches++;
+    if (g.res <= g.target || g.its >= g.maxit) {
+        g.state = Gm::DONE;
+        return BFS_OK;
     }
-    *its_out = its;
-    return status;
+    g.state = Gm::RESTART;
+    return jv_prep(c, g.u, c->d_du, 0.0, c->opt.krylov_precision, s, true);
+}
+
+// Restart, after F(u + h du) is in d_Fp: r = -F - J du, |r| into d_scal[8].
+int gm_restart_post(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    int rc = jv_post(c, g.Fbase, c->d_w, s);
+    if (rc) return rc;
+    g.jvs++;
+    k_axpby<<<grid_for(c->n), 256, 0, s>>>(c->d_w, g.F, c->d_w, c->n, -1.0, -1.0, nullptr);
+    c->launches++;
+    norms_launch(c, c->d_w, c->n, c->d_scal + 8, nullptr, s);
+    g.state = Gm::BEGIN;
+    return BFS_OK;
+}
+
+// One instance: the phases above with the residual evaluated in between.
+static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    int rc;
+    const int kp = c->opt.krylov_precision;
+    if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
+    gm_cycle_begin(c, g, c->h_pin[0], s);
+    while (g.state != Gm::DONE) {
+        if (g.state == Gm::ARNOLDI) {
+            if ((rc = gm_arnoldi_pre(c, g, s))) return rc;
+            if ((rc = residual_launch(c, c->d_up, c->d_Fp, kp, s))) return rc;
+            if ((rc = gm_arnoldi_post(c, g, s))) return rc;
+            if ((rc = read_scalars(c, c->d_scal + 8, 2, s))) return rc;
+            gm_arnoldi_host(c, g, c->h_pin[0], c->h_pin[1]);
+        } else if (g.state == Gm::CYCLE_END) {
+            if ((rc = gm_cycle_end(c, g, s))) return rc;
+        } else if (g.state == Gm::RESTART) {
+            if ((rc = residual_launch(c, c->d_up, c->d_Fp, kp, s))) return rc;
+            if ((rc = gm_restart_post(c, g, s))) return rc;
+            if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
+            gm_cycle_begin(c, g, c->h_pin[0], s);
+        } else {
+            break;
+        }
+    }
+    return g.status;
 }
 
 int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
@@ -370,13 +463,13 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
     if (rc) return rc;
     if (!c->pc_ready && (rc = precond_factor(c, c->opt.half_band, s))) return rc;
     bfs_stats S{};
-    int precs = 0, jvs = 0;
+    Gm g{};
     auto finish = [&](int status) {
         S.status = status;
         S.seconds = std::chrono::duration<double>(clk::now() - t0).count();
-        S.precond_applies = precs;
-        if (c->opt.krylov_precision == BFS_FP32C) S.residual_evals_fp32 += jvs;
-        else S.residual_evals_fp64 += jvs;
+        S.precond_applies = g.precs;
+        if (c->opt.krylov_precision == BFS_FP32C) S.residual_evals_fp32 += g.jvs;
+        else S.residual_evals_fp64 += g.jvs;
         if (st) *st = S;
         return status;
     };
@@ -395,16 +488,22 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         if (c->opt.time_budget_s > 0.0 &&
             std::chrono::duration<double>(clk::now() - t0).count() > c->opt.time_budget_s)
             return finish(BFS_ETIMEOUT);
-        int its = 0;
         // the finite difference must subtract a residual of the same arithmetic
         const double *Fbase = c->d_F;
-        if (c->opt.krylov_precision == BFS_FP32C) {
-            if ((rc = residual_launch(c, u, c->d_F32, BFS_FP32C, s))) return finish(rc);
-            S.residual_evals_fp32++;
+        if (c->opt.krylov_precision != c->opt.outer_precision) {
+            if ((rc = residual_launch(c, u, c->d_F32, c->opt.krylov_precision, s))) return finish(rc);
+            if (c->opt.krylov_precision == BFS_FP32C) S.residual_evals_fp32++;
+            else S.residual_evals_fp64++;
             Fbase = c->d_F32;
         }
-        rc = gmres(c, u, c->d_F, Fbase, f2, c->opt.eta, c->opt.max_krylov, &its, &precs, &jvs, s);
-        S.krylov_its += its;
+        Gm gk{};
+        gk.precs = g.precs;
+        gk.jvs = g.jvs;
+        gm_start(c, gk, u, c->d_F, Fbase, f2, c->opt.eta, c->opt.max_krylov, s);
+        rc = gmres(c, gk, s);
+        S.krylov_its += gk.its;
+        g.precs = gk.precs;
+        g.jvs = gk.jvs;
         if (rc) return finish(rc);
         {
             int fl = 0;

@@ -1,0 +1,307 @@
+"""Learned initial guess for the JFNK solve (spec extension).
+
+A small convolutional neural operator (the CUDA kernels behind bfs_cno_* in
+csrc/cno.cu: four dilated 3x3 convolutions, BF16 tensor-core contractions with
+FP32 accumulation) maps the bottom B = beta + 1, the Froude number and the
+node coordinates of a mesh to the nodal fields zeta, phi - x and psi - x.  Its
+output is turned into an unknown vector on the device and handed to the
+Newton iteration, which accepts it only by converging to the same tolerance;
+the uniform-stream guess remains the fallback.
+
+This module holds the ctypes binding (argument marshalling only), the
+feature construction, training-data generation with the solver itself, the
+training loop (all arithmetic in the CUDA kernels) and the A/B evaluation.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import time
+
+import numpy as np
+
+from . import bfs
+from . import workloads as W
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "cno_181x61.npz")
+_VP = ctypes.c_void_p
+
+
+def _lib():
+    L = bfs.lib()
+    if not getattr(L, "_cno_ready", False):
+        C = ctypes.POINTER
+        L.bfs_cno_num_params.restype = ctypes.c_int
+        L.bfs_cno_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, C(_VP)]
+        L.bfs_cno_destroy.argtypes = [_VP]
+        L.bfs_cno_last_error.argtypes = [_VP]
+        L.bfs_cno_last_error.restype = ctypes.c_char_p
+        L.bfs_cno_set_params.argtypes = [_VP, C(ctypes.c_float), C(ctypes.c_float)]
+        L.bfs_cno_get_params.argtypes = [_VP, C(ctypes.c_float)]
+        L.bfs_cno_forward.argtypes = [_VP, _VP, ctypes.c_int, _VP, _VP]
+        L.bfs_cno_gradient.argtypes = [_VP, _VP, _VP, ctypes.c_int, C(ctypes.c_float), C(ctypes.c_float), _VP]
+        L.bfs_cno_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP]
+        L.bfs_cno_read_loss.argtypes = [_VP, C(ctypes.c_float), _VP]
+        L.bfs_cno_guess.argtypes = [_VP, _VP, _VP, _VP, _VP]
+        L._cno_ready = True
+    return L
+
+
+# Layer shapes (must match csrc/cno.cu): (cin, cout, dilation)
+LAYERS = [(16, 32, 1), (32, 32, 3), (32, 32, 9), (32, 16, 27)]
+IN_REAL, OUT_REAL = 4, 3
+
+
+def num_params() -> int:
+    return _lib().bfs_cno_num_params()
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-style initialisation; padded input channels and unused outputs are 0."""
+    rng = np.random.default_rng(W.SEED_BASE + 500 + seed)
+    out = []
+    for li, (cin, cout, _) in enumerate(LAYERS):
+        real_in = IN_REAL if li == 0 else cin
+        std = math.sqrt(2.0 / (9 * real_in)) * (0.5 if li == len(LAYERS) - 1 else 1.0)
+        w = rng.standard_normal((cout, 9, cin)) * std
+        if li == 0:
+            w[:, :, IN_REAL:] = 0.0
+        if li == len(LAYERS) - 1:
+            w[OUT_REAL:, :, :] = 0.0
+        out.append(w.ravel())
+        out.append(np.zeros(cout))
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == num_params()
+    return p
+
+
+class CNO:
+    def __init__(self, H: int, Wd: int, batch_max: int = 16):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA device required")
+        h = _VP()
+        rc = _lib().bfs_cno_create(H, Wd, batch_max, ctypes.byref(h))
+        if rc:
+            raise bfs.BfsError(rc, _lib().bfs_cno_last_error(None).decode())
+        self._n = h
+        self.H, self.W, self.batch_max = H, Wd, batch_max
+        self.np = num_params()
+        self.scale = np.ones(3, dtype=np.float32)
+
+    def _check(self, rc):
+        if rc:
+            raise bfs.BfsError(rc, _lib().bfs_cno_last_error(self._n).decode())
+
+    def close(self):
+        if getattr(self, "_n", None):
+            _lib().bfs_cno_destroy(self._n)
+            self._n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p: np.ndarray, scale=None):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.np
+        if scale is not None:
+            self.scale = np.ascontiguousarray(scale, dtype=np.float32)
+        F = ctypes.POINTER(ctypes.c_float)
+        self._check(_lib().bfs_cno_set_params(self._n, p.ctypes.data_as(F), self.scale.ctypes.data_as(F)))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.np, dtype=np.float32)
+        self._check(_lib().bfs_cno_get_params(self._n, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    def forward(self, x):
+        """x: CUDA float32 [Bt, H, W, 4] -> CUDA float32 [Bt, H, W, 16]."""
+        import torch
+        Bt = x.shape[0]
+        y = torch.empty((Bt, self.H, self.W, 16), dtype=torch.float32, device="cuda")
+        self._check(_lib().bfs_cno_forward(self._n, _VP(x.data_ptr()), Bt, _VP(y.data_ptr()), bfs._stream(None)))
+        return y
+
+    def gradient(self, x, t):
+        g = np.empty(self.np, dtype=np.float32)
+        loss = ctypes.c_float()
+        F = ctypes.POINTER(ctypes.c_float)
+        self._check(_lib().bfs_cno_gradient(self._n, _VP(x.data_ptr()), _VP(t.data_ptr()), x.shape[0],
+                                            g.ctypes.data_as(F), ctypes.byref(loss), bfs._stream(None)))
+        return g, loss.value
+
+    def train_step(self, x, t, lr: float):
+        self._check(_lib().bfs_cno_train_step(self._n, _VP(x.data_ptr()), _VP(t.data_ptr()), x.shape[0],
+                                              float(lr), bfs._stream(None)))
+
+    def loss(self) -> float:
+        v = ctypes.c_float()
+        self._check(_lib().bfs_cno_read_loss(self._n, ctypes.byref(v), bfs._stream(None)))
+        return v.value
+
+    def guess(self, ctx: bfs.Context, x, u=None):
+        """Unknown vector for ctx from features x (CUDA float32 [1, M, N, 4])."""
+        import torch
+        if u is None:
+            u = torch.empty(ctx.n, dtype=torch.float64, device="cuda")
+        self._check(_lib().bfs_cno_guess(self._n, ctx._ctx, _VP(x.data_ptr()), _VP(u.data_ptr()),
+                                         bfs._stream(None)))
+        return u
+
+
+def features(mesh, topo, F: float) -> np.ndarray:
+    """Input channels on the nodal grid, [M, N, 4]: B / 0.3, (F - 0.95) / 0.45 and
+    the node coordinates scaled to [-1, 1]."""
+    X, Y = np.meshgrid(mesh.x(), mesh.y())
+    B = (topo.beta + 1.0).reshape(mesh.M, mesh.N)
+    xs = (X - 0.5 * (X.max() + X.min())) / (0.5 * (X.max() - X.min()))
+    ys = (Y - 0.5 * (Y.max() + Y.min())) / max(1e-12, 0.5 * (Y.max() - Y.min()))
+    f = np.stack([B / 0.3, np.full_like(B, (F - 0.95) / 0.45), xs, ys], axis=-1)
+    return f.astype(np.float32)
+
+
+def sample_problem(rng, mesh):
+    """One draw of the batched-sweep distribution (F, bumps or a ridge) on `mesh`."""
+    F = float(rng.uniform(0.5, 1.4))
+    if rng.uniform() < 0.8:
+        nb = int(rng.integers(1, 4))
+        bumps = [(float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)),
+                  float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2))) for _ in range(nb)]
+        return W.gaussian_bumps(mesh, bumps), F
+    return W.gaussian_bumps(mesh, [], ridges=[(float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)),
+                                               float(rng.uniform(-2, 2)))]), F
+
+
+def scaled(topo, s: float):
+    """The bottom with every bump height multiplied by s (beta + 1 scales linearly)."""
+    return W.Topography(-1.0 + s * (topo.beta + 1.0), s * topo.beta_x, s * topo.beta_y)
+
+
+def solve_with_continuation(ctx, topo, u0=None, stages=(1.0 / 3.0, 2.0 / 3.0, 1.0), direct_first=True):
+    """Solve on ctx for `topo`: first directly from u0 (the uniform stream when
+    None), and if that fails by continuation in bump height through `stages`,
+    each stage starting from the previous solution (the paper's route to large
+    amplitudes).  Returns (u, status, cost) with cost = summed Newton and Krylov
+    iterations, residual evaluations and stages used."""
+    cost = {"newton": 0, "krylov": 0, "evals": 0, "stages": 0}
+
+    def add(st):
+        cost["newton"] += st["newton_its"]
+        cost["krylov"] += st["krylov_its"]
+        cost["evals"] += st["residual_evals_fp64"] + st["residual_evals_fp32"]
+        cost["stages"] += 1
+
+    if direct_first:
+        ctx.set_topography(topo)
+        u = ctx.flat_guess() if u0 is None else u0.clone()
+        st = ctx.solve(u, raise_on_error=False)
+        add(st)
+        if st["status"] == 0:
+            return u, 0, cost
+    u = ctx.flat_guess()
+    status = -1
+    for sfac in stages:
+        ctx.set_topography(scaled(topo, sfac))
+        st = ctx.solve(u, raise_on_error=False)
+        add(st)
+        status = st["status"]
+        if status != 0:
+            break
+    return u, status, cost
+
+
+def bin_context(ctxs, mesh, topo, F, opts, bin_width=0.02):
+    """A context for F from the per-bin cache (one factored preconditioner per
+    bin of Froude numbers; F itself is set exactly)."""
+    key = int(F / bin_width)
+    if key not in ctxs:
+        c = bfs.Context(mesh, topo, (key + 0.5) * bin_width, opts)
+        c.precond_factor()
+        ctxs[key] = c
+    c = ctxs[key]
+    c.set_froude(F)
+    return c
+
+
+def solver_options(tol: float = 1e-8, budget_s: float = 3.0):
+    return bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
+                               eta=1e-2, max_newton=25, max_krylov=200, time_budget_s=budget_s)
+
+
+def generate(n: int, seed: int, mesh=None, tol: float = 1e-8, log=None):
+    """Solve n problems drawn from the batched-sweep distribution on `mesh`
+    (default 181 x 61), directly or by continuation in bump height.  Returns
+    (features [n, M, N, 4], targets [n, M, N, 3] = zeta, phi - x, psi - x,
+    records)."""
+    import torch
+    mesh = mesh or W.config_paper_scale()[0]
+    rng = np.random.default_rng(W.SEED_BASE + 7000 + seed)
+    probs = [sample_problem(rng, mesh) for _ in range(n)]
+    xs = np.zeros((n, mesh.M, mesh.N, 4), dtype=np.float32)
+    ys = np.zeros((n, mesh.M, mesh.N, 3), dtype=np.float32)
+    recs, ctxs = [], {}
+    opts = solver_options(tol)
+    xg = torch.tensor(mesh.x(), device="cuda").view(1, -1)
+    t0 = time.time()
+    for i, (topo, F) in enumerate(probs):
+        c = bin_context(ctxs, mesh, topo, F, opts)
+        u, status, cost = solve_with_continuation(c, topo)
+        recs.append({"F": F, "status": status, **cost})
+        xs[i] = features(mesh, topo, F)
+        if status == 0:
+            nv = c.unpack(u)
+            ys[i, :, :, 0] = nv["zeta"].float().cpu().numpy()
+            ys[i, :, :, 1] = (nv["phi"] - xg).float().cpu().numpy()
+            ys[i, :, :, 2] = (nv["psi"] - xg).float().cpu().numpy()
+        if log and (i + 1) % 50 == 0:
+            ok = sum(r["status"] == 0 for r in recs)
+            log(f"generated {i + 1}/{n} ({ok} converged) in {time.time() - t0:.1f} s")
+    for c in ctxs.values():
+        c.close()
+    return xs, ys, recs
+
+
+def train(xs, ys, epochs: int = 60, batch: int = 16, lr: float = 2e-3, seed: int = 0, log=None):
+    """Adam on the mean squared error of the scaled targets; returns (params,
+    scale, losses).  Only converged samples should be passed."""
+    import torch
+    n, H, Wd, _ = xs.shape
+    scale = np.maximum(ys.reshape(-1, 3).std(axis=0), 1e-6).astype(np.float32)
+    net = CNO(H, Wd, batch)
+    net.set_params(init_params(seed), scale)
+    X = torch.tensor(xs, device="cuda")
+    T = torch.tensor(ys / scale, device="cuda")
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    batch = max(1, min(batch, n))
+    steps = epochs * max(1, n // batch)
+    losses, k = [], 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g)
+        ep_loss = []
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch].cuda()
+            lr_k = lr * 0.5 * (1 + math.cos(math.pi * k / steps))
+            net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr_k)
+            k += 1
+            if b0 == 0 or b0 + 2 * batch > n:
+                ep_loss.append(net.loss())
+        losses.append(float(np.mean(ep_loss)))
+        if log and (ep % 10 == 0 or ep == epochs - 1):
+            log(f"epoch {ep}: loss {losses[-1]:.4e}")
+    p = net.get_params()
+    net.close()
+    return p, scale, losses
+
+
+def save(path, params, scale, meta: dict):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, params=params, scale=scale, **{k: np.asarray(v) for k, v in meta.items()})
+
+
+def load(path=WEIGHTS):
+    d = np.load(path)
+    return d["params"], d["scale"]

@@ -166,3 +166,33 @@ def mesh_box(N: int, M: int, dx: float, dy: float, half: int = 0, x1: float | No
         x1 = -round(0.28 * (N - 1)) * dx
     y1 = 0.0 if half else -0.5 * (M - 1) * dy
     return Mesh(N=N, M=M, x1=x1, y1=y1, dx=dx, dy=dy, half=half)
+
+
+def config_batch(seed: int = 3, B: int = 64, sizes=None):
+    """Batched-sweep workload: B instances with F ~ U[0.5, 1.4]; the bottom is
+    1-3 Gaussians (eps ~ U[0.05, 0.3], delta ~ U[0.5, 2], centres ~ U[-2, 2]^2)
+    or a cross-stream ridge (a ~ U[0.05, 0.3], width ~ U[0.5, 2], x_r ~ U[-2, 2]);
+    meshes N in {61, 81, ..., 241}, M = (N - 1)/3 + 1, dx = dy = 0.3, full
+    domain.  `sizes` overrides the list of N (tests use small meshes).
+    Returns (meshes, topographies, Froude numbers)."""
+    rng = np.random.default_rng(SEED_BASE + seed)
+    Ns = list(sizes) if sizes is not None else list(range(61, 242, 20))
+    meshes, topos, Fs = [], [], []
+    for _ in range(B):
+        N = int(rng.choice(Ns))
+        M = (N - 1) // 3 + 1
+        mesh = mesh_box(N, M, 0.3, 0.3)
+        F = float(rng.uniform(0.5, 1.4))
+        if rng.uniform() < 0.8:
+            nb = int(rng.integers(1, 4))
+            bumps = [(float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)),
+                      float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2))) for _ in range(nb)]
+            topo = gaussian_bumps(mesh, bumps)
+        else:
+            topo = gaussian_bumps(mesh, [], ridges=[(float(rng.uniform(0.05, 0.3)),
+                                                     float(rng.uniform(0.5, 2.0)),
+                                                     float(rng.uniform(-2, 2)))])
+        meshes.append(mesh)
+        topos.append(topo)
+        Fs.append(F)
+    return meshes, topos, Fs

@@ -254,3 +254,25 @@ def test_paper_scale_mixed_solve_is_a_root(F):
     z1 = O.nodal_values(P, ug)["zeta"]
     z2 = O.nodal_values(P, u64.cpu().numpy())["zeta"]
     assert np.abs(z1 - z2).max() <= 1e-6
+
+
+def test_set_topography_and_froude_keep_the_preconditioner():
+    """Continuation in bump height (the preconditioner does not depend on the
+    bottom) and a Froude-number change (the old factorisation is kept as an
+    approximation): both solves reach roots the oracle accepts."""
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, F = W.config_small_half()
+    ctx = _ctx(mesh, topo, F, tol=1e-10)
+    u = ctx.flat_guess()
+    assert ctx.solve(u)["status"] == 0
+    bigger = W.gaussian_bumps(mesh, [(0.2, 1.0 / math.sqrt(2.0), 0.0, 0.0)])
+    ctx.set_topography(bigger)
+    st = ctx.solve(u)  # continue from the eps = 0.1 solution
+    assert st["status"] == 0
+    assert np.abs(O.residual(O.problem(mesh, F), bigger, u.cpu().numpy())).max() <= 1e-10
+    ctx.set_froude(0.75)
+    st = ctx.solve(u)
+    assert st["status"] == 0
+    assert np.abs(O.residual(O.problem(mesh, 0.75), bigger, u.cpu().numpy())).max() <= 1e-10
+    with pytest.raises(bfs.BfsError):
+        ctx.set_froude(0.0)
