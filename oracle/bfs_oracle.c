@@ -58,6 +58,9 @@ typedef struct {
     double F;              /* depth-based Froude number (Sec. 2.1) */
     double n_rad;          /* upstream decay rate n of the radiation condition */
     double sigma;          /* sign of the bottom single layer I4 (R4) */
+    const double *psurf;   /* applied surface pressure at the nodes, or NULL
+                              (the pressure-distribution problem of Sec. 4.1:
+                              p adds to the dynamic condition) */
 } orc_problem;
 
 typedef struct {
@@ -324,7 +327,8 @@ static void orc_radiation(const orc_problem *P, const orc_nodal *nd, double *Fv,
     }
 }
 
-/* Combined dynamic condition at a half point (Sec. 2.1, combined dynamic condition). */
+/* Combined dynamic condition at a half point (Sec. 2.1, combined dynamic
+   condition); an applied surface pressure p* enters as + p* (Sec. 4.1). */
 static double orc_bernoulli(double F, double z, double zx, double zy, double px, double py,
                             double *sc)
 {
@@ -370,6 +374,11 @@ void orc_residual(const orc_problem *P, const double *beta, const double *bx, co
         double J = orc_bie_point(P, &top, &bot, 1, &Tb, &sc7);
         Fout[orc_row_F7(P, k, l)] = J - 2.0 * ORC_PI * gs;
         Fout[orc_row_F1(P, k, l)] = orc_bernoulli(P->F, zs, zxs, zys, pxs, pys, &sc1);
+        if (P->psurf) {
+            double pstar = 0.5 * (P->psurf[a] + P->psurf[b]);
+            Fout[orc_row_F1(P, k, l)] += pstar;
+            sc1 += fabs(pstar);
+        }
         if (scale) {
             scale[orc_row_F2(P, k, l)] = sc2 + 2.0 * ORC_PI * fabs(fs);
             scale[orc_row_F7(P, k, l)] = sc7 + 2.0 * ORC_PI * fabs(gs);
@@ -770,4 +779,43 @@ int orc_newton_dense(const orc_problem *P, const double *beta, const double *bx,
     st->status = status;
     free(J); free(piv); free(Fv); free(du); free(ut); free(Ft);
     return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Pressure on the bottom (Sec. 2.1: Bernoulli's equation along the    */
+/* bottom, with the bottom kinematic condition folded in, written for   */
+/* psi the bottom potential) and the force of the fluid on the          */
+/* topography, integral of p (beta_x, beta_y, -1) dx dy by the          */
+/* trapezoid rule (the outward normal of the fluid on the bottom times  */
+/* dS is (beta_x, beta_y, -1) dx dy).  p: N*M nodal values; force: 3.   */
+/* The half domain counts the mirror image of every row but y = 0 and   */
+/* gives force[1] = 0.                                                  */
+/* ------------------------------------------------------------------ */
+void orc_bottom_pressure(const orc_problem *P, const double *beta, const double *bx,
+                         const double *by, const double *u, double *p, double *force)
+{
+    int N = P->N, M = P->M;
+    size_t n = (size_t)N * M;
+    double *ps = (double *)malloc(n * sizeof(double)), *psx = (double *)malloc(n * sizeof(double));
+    double *psy = (double *)malloc(n * sizeof(double));
+    orc_unpack_field(P, u, 2, ps, psx);
+    orc_ydiff(P, ps, psy);
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int j = 0; j < M; j++)
+        for (int i = 0; i < N; i++) {
+            size_t q = (size_t)j * N + i;
+            double a = bx[q], b = by[q], gx = psx[q], gy = psy[q];
+            double kin = 0.5 * ((1.0 + a * a) * gy * gy + (1.0 + b * b) * gx * gx - 2.0 * a * b * gx * gy) /
+                         (1.0 + a * a + b * b);
+            double pv = 0.5 - kin - beta[q] / (P->F * P->F);
+            p[q] = pv;
+            double w = orc_weight(P, i, j) * ((P->half && j > 0) ? 2.0 : 1.0);
+            fx += w * pv * a;
+            fy += w * pv * b;
+            fz -= w * pv;
+        }
+    force[0] = fx;
+    force[1] = P->half ? 0.0 : fy;
+    force[2] = fz;
+    free(ps); free(psx); free(psy);
 }

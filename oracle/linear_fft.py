@@ -73,3 +73,20 @@ def dispersion_k(F: float, psi: float = 0.0) -> float:
         else:
             hi = mid
     return 0.5 * (lo + hi)
+
+
+def equivalent_pressure(b_func, F: float, xq, yq, L: float = 204.8, h: float = 0.1):
+    """The surface pressure whose linear wave pattern equals that of the bottom
+    perturbation b = beta + 1 (Sec. 4.1): p^ = sech(k) b^ / F^2 in the
+    convention of zeta_linear (the paper writes sech(k) beta~ / (eps F^2) with
+    its own scaling of p).  With it, the linear surfaces satisfy
+    zeta_bump = zeta_pressure + F^2 p.  Sampled at the grid points xq, yq."""
+    n = int(round(L / h))
+    x = (np.arange(n) - n // 2) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    bh = np.fft.fft2(b_func(X, Y))
+    a = 2.0 * np.pi * np.fft.fftfreq(n, d=h)
+    k = np.sqrt(a[None, :] ** 2 + a[:, None] ** 2)
+    ph = bh / np.cosh(np.minimum(k, 350.0)) / (F * F)
+    p = np.real(np.fft.ifft2(ph))
+    return sample(x, x, p, xq, yq)

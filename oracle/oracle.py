@@ -14,6 +14,9 @@ Parity status of each function (how it is pinned, see tests/test_oracle_pins.py)
   residual_linear / jtilde ... App. B printed entries that are self-consistent,
                        block symmetries J23 = J32, J22 = J33 (Sec. 4.2)
   lu / jfnk / newton_dense ... dense solve vs numpy; JFNK vs dense FD Newton
+  bottom_pressure .... hydrostatic value at the uniform stream; Bernoulli on a
+                       streamsurface of a linear potential; force = 0 with
+                       no bottom slope
 """
 from __future__ import annotations
 
@@ -46,7 +49,7 @@ class Problem(ctypes.Structure):
                 ("x1", ctypes.c_double), ("y1", ctypes.c_double),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("F", ctypes.c_double), ("n_rad", ctypes.c_double),
-                ("sigma", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("psurf", ctypes.POINTER(ctypes.c_double))]
 
 
 class Stats(ctypes.Structure):
@@ -96,6 +99,7 @@ def lib():
             L.orc_newton_dense.argtypes = [P, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int,
                                            ctypes.POINTER(Stats)]
             L.orc_newton_dense.restype = ctypes.c_int
+            L.orc_bottom_pressure.argtypes = [P, _D, _D, _D, _D, _D, _D]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -110,9 +114,15 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def problem(mesh, F: float, sigma: float = -1.0, n_rad: float = 0.05) -> Problem:
-    return Problem(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy,
-                   float(F), float(n_rad), float(sigma))
+def problem(mesh, F: float, sigma: float = -1.0, n_rad: float = 0.05, psurf=None) -> Problem:
+    """psurf: optional applied surface pressure at the nodes (kept alive on the
+    returned structure)."""
+    P = Problem(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy,
+                float(F), float(n_rad), float(sigma), None)
+    if psurf is not None:
+        P._psurf = _f64(psurf).ravel().copy()
+        P.psurf = _p(P._psurf)
+    return P
 
 
 def num_threads() -> int:
@@ -187,6 +197,15 @@ def bie_point(P: Problem, top: dict, bot: dict, self_bottom: bool, target: dict)
     v = lib().orc_bie_point(ctypes.byref(P), ctypes.byref(st), ctypes.byref(sb),
                             int(bool(self_bottom)), ctypes.byref(T), ctypes.byref(sc))
     return v, sc.value
+
+
+def bottom_pressure(P: Problem, topo, u):
+    """Nodal bottom pressure (M x N) and the force (3,) on the topography."""
+    b, bx, by, u = _f64(topo.beta), _f64(topo.beta_x), _f64(topo.beta_y), _f64(u)
+    p = np.empty(P.N * P.M)
+    f = np.empty(3)
+    lib().orc_bottom_pressure(ctypes.byref(P), _p(b), _p(bx), _p(by), _p(u), _p(p), _p(f))
+    return p.reshape(P.M, P.N), f
 
 
 def lu_solve_dense(A: np.ndarray, b: np.ndarray) -> np.ndarray:

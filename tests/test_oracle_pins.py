@@ -426,3 +426,70 @@ def test_dense_lu_against_numpy():
     A = rng.standard_normal((40, 40)) + 10 * np.eye(40)
     b = rng.standard_normal(40)
     assert np.allclose(O.lu_solve_dense(A, b), np.linalg.solve(A, b), rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Bottom pressure (Sec. 2.1): hydrostatic at the uniform stream; on a bottom
+# plane that is a streamsurface of Phi = x + b y + a z, p = 1/2 - |grad Phi|^2/2
+# - beta/F^2; the force integrates p (beta_x, beta_y, -1) dx dy.
+# ---------------------------------------------------------------------------
+def test_bottom_pressure_uniform_stream_is_hydrostatic():
+    mesh = W.mesh_box(15, 7, 0.4, 0.4)
+    F = 0.8
+    P = O.problem(mesh, F)
+    p, f = O.bottom_pressure(P, W.flat_topography(mesh), W.flat_guess(mesh))
+    assert np.abs(p - 1.0 / F ** 2).max() < 1e-12
+    area = (mesh.N - 1) * mesh.dx * (mesh.M - 1) * mesh.dy
+    assert abs(f[0]) < 1e-12 and abs(f[1]) < 1e-12
+    assert abs(f[2] + area / F ** 2) < 1e-9 * area
+
+
+def test_bottom_pressure_on_streamsurface_plane():
+    mesh = W.Mesh(N=11, M=7, x1=-2.0, y1=-0.9, dx=0.4, dy=0.3)
+    F, a, b, q = 0.8, 0.05, -0.04, 0.1
+    pp = a - b * q  # plane beta = -1.2 + pp x + q y (below z = 0 on this machine)
+    P = O.problem(mesh, F)
+    X, Y = np.meshgrid(mesh.x(), mesh.y())
+    beta = -1.2 + pp * X + q * Y
+    topo = W.Topography(beta.ravel(), np.full(beta.size, pp), np.full(beta.size, q))
+    per, blk = mesh.N + 1, (mesh.N + 1) * mesh.M
+    u = W.flat_guess(mesh)
+    for j, yj in enumerate(mesh.y()):
+        # psi = Phi on the plane = (1 + a pp) x + (b + a q) y + a (-1.2)
+        u[2 * blk + j * per] = (1 + a * pp) * mesh.x1 + (b + a * q) * yj - 1.2 * a
+        u[2 * blk + j * per + 1: 2 * blk + (j + 1) * per] = 1 + a * pp
+    p, f = O.bottom_pressure(P, topo, u)
+    expect = 0.5 - 0.5 * (1 + a * a + b * b) - beta / F ** 2
+    assert np.abs(p - expect).max() < 1e-12
+    # force components with the trapezoid rule on this plane
+    wts = np.outer(np.where((np.arange(mesh.M) == 0) | (np.arange(mesh.M) == mesh.M - 1), 0.5, 1.0),
+                   np.where((np.arange(mesh.N) == 0) | (np.arange(mesh.N) == mesh.N - 1), 0.5, 1.0))
+    wts = wts * mesh.dx * mesh.dy
+    assert abs(f[0] - np.sum(wts * expect * pp)) < 1e-12
+    assert abs(f[2] + np.sum(wts * expect)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.1: a surface pressure with p^ = sech(k) b^ / F^2 gives, in the linear
+# regime, the bump's wave pattern: zeta_pressure = zeta_bump - F^2 p.  Two
+# independent forcing paths of the oracle (bottom integrals vs the dynamic
+# condition) must agree through that relation at small amplitude.
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+def test_pressure_patch_matches_bump_in_linear_regime():
+    F, eps = 0.7, 1e-3
+    errs = []
+    for dx in (0.4, 0.3):
+        N, M = int(round(12.0 / dx)) + 1, int(round(3.6 / dx)) + 1
+        mesh = W.Mesh(N=N, M=M, x1=-4.8, y1=0.0, dx=dx, dy=dx, half=1)
+        bf = lambda X, Y: eps * np.exp(-(X * X + Y * Y))
+        topo = W.gaussian_bumps(mesh, [(eps, 1 / math.sqrt(2), 0.0, 0.0)])
+        ub, sb = O.jfnk(O.problem(mesh, F), topo, W.flat_guess(mesh), tol=1e-12)
+        p = LF.equivalent_pressure(bf, F, mesh.x(), mesh.y())
+        up, sp = O.jfnk(O.problem(mesh, F, psurf=p), W.flat_topography(mesh), W.flat_guess(mesh), tol=1e-12)
+        assert sb["status"] == 0 and sp["status"] == 0
+        zb = O.nodal_values(O.problem(mesh, F), ub)["zeta"]
+        zp = O.nodal_values(O.problem(mesh, F), up)["zeta"]
+        pred = zb - F * F * p
+        errs.append(np.abs(zp - pred).max() / np.abs(pred).max())
+    assert errs[0] < 1e-2 and errs[1] < errs[0]
