@@ -36,6 +36,11 @@ UNIT = "pair-evals/s"
 INSTR_PER_INDEX_PAIR = 51
 
 
+def _pc_prec(args):
+    from paper_1709_08803_gb300 import bfs
+    return bfs.BFS_FP32C if args.precond == "fp32" else bfs.BFS_FP64
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -205,7 +210,8 @@ def run_batch(args):
     __graft_entry__.build()
     meshes, topos, Fs = W.config_batch(seed=3, B=args.batch)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=args.eta, max_newton=30, max_krylov=150, time_budget_s=60.0)
+                               eta=args.eta, max_newton=30, max_krylov=150, time_budget_s=60.0,
+                               precond_precision=_pc_prec(args))
     t0 = time.perf_counter()
     b = bfs.Batch(meshes, topos, Fs, opts)
     setup_s = time.perf_counter() - t0
@@ -274,6 +280,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--F", type=float, default=0.7)
     ap.add_argument("--eta", type=float, default=1e-2)
+    ap.add_argument("--precond", default="fp32", choices=["fp32", "fp64"],
+                    help="storage/arithmetic of the preconditioner sweeps in the mixed form")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch"],
@@ -306,7 +314,7 @@ def main():
 
     mesh, topo, F = W.config_paper_scale(args.F)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=args.eta)
+                               eta=args.eta, precond_precision=_pc_prec(args))
     ctx = bfs.Context(mesh, topo, F, opts)
     pairs_per_residual = ctx.pair_evals
     n_index_pairs = mesh.n_targets * mesh.n_sources
@@ -415,10 +423,13 @@ def main():
     h = int(opts.half_band if opts.half_band > 0 else max(1, round(mesh.M / 20)))
     nb = 3 * (mesh.N + 1)
     blocks = sum(min(k, h) + 1 + min(mesh.M - 1 - k, h) for k in range(mesh.M))
-    apply_bytes = blocks * nb * nb * 8 + 6 * ctx.n * 8
+    esz = 4 if args.precond == "fp32" else 8
+    apply_bytes = blocks * nb * nb * esz + 6 * ctx.n * 8
     avg_ap = msap / max(nap, 1)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    roofline_apply = {"bound": "hbm", "kernel": "k_apply_coop (block-banded LU sweeps)",
+    roofline_apply = {"bound": "hbm", "kernel": f"k_apply_split<{'float' if esz == 4 else 'double'}> (block-banded LU sweeps)",
+                      "sweep_steps": 2 * mesh.M,
+                      "us_per_sweep_step": avg_ap * 1e3 / (2 * mesh.M) if nap else None,
                       "achieved": apply_bytes / (avg_ap / 1e3) / 1e9 if nap else None, "peak": hbm,
                       "unit": "GB/s", "frac": (apply_bytes / (avg_ap / 1e3) / 1e9) / hbm if nap else None,
                       "traffic": None, "algorithmic_bytes": apply_bytes, "avg_launch_ms": avg_ap,
@@ -446,7 +457,8 @@ def main():
                                        "solve from the uniform stream to |F|inf<=1e-8" % F,
                            "form": "mixed: FP32C residuals inside Jv; Newton residual and line search in "
                                    "double-float (FP64-accurate, 1e-10 per-row parity); FP64 GMRES and "
-                                   "banded LU; no learned guess",
+                                   "banded-LU factorisation; preconditioner sweeps in %s; no learned "
+                                   "guess" % ("FP32 over FP32 copies of the factors" if args.precond == "fp32" else "FP64"),
                            "l2": "flushed between steps (256 MiB write); sources fit in L2",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "precond_half_band": int(opts.half_band if opts.half_band > 0 else max(1, round(mesh.M / 20))),

@@ -94,6 +94,11 @@ typedef struct {
     int src_splits;       /* source splits of the pair kernels (<= 0: automatic) */
     int outer_precision;  /* BFS_FP64 (default) or BFS_DF64 for the Newton residual
                              and the line search */
+    int precond_precision; /* BFS_FP64 (default) or BFS_FP32C: storage and arithmetic
+                              of the preconditioner sweeps.  The factorisation is FP64
+                              either way; FP32C sweeps an FP32 copy of the factors
+                              (the preconditioner only steers GMRES, the Newton
+                              residual and the converged u do not depend on it) */
 } bfs_options;
 
 typedef struct {
@@ -131,6 +136,14 @@ void bfs_destroy(bfs_ctx *ctx);
    paper's large-amplitude solutions rely on (Sec. 5).  Synchronous; errors as
    bfs_setup's topography checks. */
 int bfs_set_topography(bfs_ctx *ctx, const bfs_topo *topo);
+
+/* Apply a pressure distribution p(x, y) to the free surface (the ship-wake
+   model the paper relates to the bump in Sec. 4.1 and 6): p adds to the
+   combined dynamic condition, p* being the mean of the two nodes around each
+   half point.  p: HOST array of N*M nodal values (index i + N*j), copied; NULL
+   removes it.  The preconditioner is unchanged (p does not depend on u).
+   Synchronous; BFS_EINVAL for a non-finite value. */
+int bfs_set_surface_pressure(bfs_ctx *ctx, const double *p);
 
 /* Change the Froude number.  The factored preconditioner (formed for the
    previous F) is kept as an approximation and stays usable; call
@@ -194,6 +207,15 @@ int bfs_flat_guess(bfs_ctx *ctx, double *u, void *stream);
    (index i + N*j): zeta, zeta_x, zeta_y, phi, phi_x, phi_y, psi, psi_x
    (trapezoid reconstruction in x, second-order differences in y). */
 int bfs_unpack(bfs_ctx *ctx, const double *u, double *out, void *stream);
+
+/* Pressure on the bottom and the force of the fluid on the topography
+   (Sec. 2.1: Bernoulli's equation along the bottom, from the bottom potential
+   psi of u).  u: device vector; p: device array of N*M nodal pressures (index
+   i + N*j); force_host (may be NULL): 3 host doubles, the trapezoid integral of
+   p (beta_x, beta_y, -1) dx dy (x: drag, z: vertical; the half domain reports
+   the whole mirrored domain and a zero y component).  Synchronous when
+   force_host is given. */
+int bfs_bottom_pressure(bfs_ctx *ctx, const double *u, double *p, double *force_host, void *stream);
 
 /* Profiling.  bfs_profile_enable(ctx, 1) records a CUDA event pair on the
    launching stream around every pair-kernel launch and every preconditioner

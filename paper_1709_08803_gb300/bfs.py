@@ -50,7 +50,7 @@ class bfs_options(ctypes.Structure):
                 ("max_krylov", ctypes.c_int), ("eta", ctypes.c_double),
                 ("krylov_precision", ctypes.c_int), ("jv_h_rel", ctypes.c_double),
                 ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
-                ("outer_precision", ctypes.c_int)]
+                ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int)]
 
 
 class bfs_stats(ctypes.Structure):
@@ -116,8 +116,10 @@ def lib():
         L.bfs_batch_tuning.argtypes = [_VP, C(ctypes.c_int), C(ctypes.c_int), C(ctypes.c_int),
                                        C(ctypes.c_double)]
         L.bfs_batch_solve.argtypes = [_VP, C(_VP), C(bfs_stats), _VP]
+        L.bfs_bottom_pressure.argtypes = [_VP, _VP, _VP, C(ctypes.c_double), _VP]
         L.bfs_set_topography.argtypes = [_VP, C(bfs_topo)]
         L.bfs_set_froude.argtypes = [_VP, ctypes.c_double]
+        L.bfs_set_surface_pressure.argtypes = [_VP, _VP]
         L.bfs_profile_enable.argtypes = [_VP, ctypes.c_int]
         L.bfs_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_ulonglong)]
@@ -254,11 +256,28 @@ class Context:
         self._check(lib().bfs_flat_guess(self._ctx, self._vec(out), _stream(stream)))
         return out
 
+    def bottom_pressure(self, u, stream=None):
+        """(nodal bottom pressure [M, N] on the device, force (3,) on the host)."""
+        import torch
+        p = torch.empty(self.mesh.N * self.mesh.M, dtype=torch.float64, device="cuda")
+        f = (ctypes.c_double * 3)()
+        self._check(lib().bfs_bottom_pressure(self._ctx, self._vec(u), ctypes.c_void_p(_ptr(p)), f,
+                                              _stream(stream)))
+        return p.view(self.mesh.M, self.mesh.N), np.array(list(f))
+
     def set_topography(self, topo):
         self._h = [np.ascontiguousarray(a, dtype=np.float64) for a in (topo.beta, topo.beta_x, topo.beta_y)]
         D = ctypes.POINTER(ctypes.c_double)
         t = bfs_topo(*[a.ctypes.data_as(D) for a in self._h])
         self._check(lib().bfs_set_topography(self._ctx, ctypes.byref(t)))
+
+    def set_surface_pressure(self, p=None):
+        if p is None:
+            self._check(lib().bfs_set_surface_pressure(self._ctx, None))
+            return
+        self._p = np.ascontiguousarray(p, dtype=np.float64).ravel()
+        assert self._p.size == self.mesh.N * self.mesh.M
+        self._check(lib().bfs_set_surface_pressure(self._ctx, ctypes.c_void_p(self._p.ctypes.data)))
 
     def set_froude(self, F: float):
         self._check(lib().bfs_set_froude(self._ctx, float(F)))

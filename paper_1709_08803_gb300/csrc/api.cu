@@ -34,6 +34,7 @@ void free_all(bfs_ctx *c)
     cudaFree(c->d_tgtdf);
     cudaFree(c->d_part);
     cudaFree(c->d_constB);
+    cudaFree(c->d_psurf);
     cudaFree(c->d_flag);
     cudaFree(c->d_up);
     cudaFree(c->d_scal);
@@ -83,6 +84,7 @@ void bfs_default_options(bfs_options *o)
     o->time_budget_s = 0.0;
     o->src_splits = 0;
     o->outer_precision = BFS_FP64;
+    o->precond_precision = BFS_FP64;
 }
 
 const char *bfs_last_error(const bfs_ctx *c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -117,6 +119,8 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
         return set_err(nullptr, BFS_EINVAL, "sign_I4 must be +1 or -1");
     if (o.krylov_precision != BFS_FP64 && o.krylov_precision != BFS_FP32C && o.krylov_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "unknown krylov_precision");
+    if (o.precond_precision != BFS_FP64 && o.precond_precision != BFS_FP32C)
+        return set_err(nullptr, BFS_EINVAL, "precond_precision must be BFS_FP64 or BFS_FP32C");
     if (o.outer_precision != BFS_FP64 && o.outer_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "outer_precision must be BFS_FP64 or BFS_DF64");
     const size_t NM = (size_t)N * M;
@@ -210,6 +214,25 @@ int bfs_set_topography(bfs_ctx *c, const bfs_topo *topo)
     return BFS_OK;
 }
 
+int bfs_set_surface_pressure(bfs_ctx *c, const double *p)
+{
+    if (!c) return BFS_EINVAL;
+    if (!p) {
+        cudaFree(c->d_psurf);
+        c->d_psurf = nullptr;
+        return BFS_OK;
+    }
+    for (int q = 0; q < c->NM; q++)
+        if (!isfinite(p[q])) return set_err(c, BFS_EINVAL, "surface pressure has a non-finite value");
+    BFS_CUDA_TRY(c, cudaDeviceSynchronize());
+    if (!c->d_psurf && cudaMalloc(&c->d_psurf, sizeof(double) * (size_t)c->NM) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, BFS_ENOMEM, "device allocation failed");
+    }
+    BFS_CUDA_TRY(c, cudaMemcpy(c->d_psurf, p, sizeof(double) * (size_t)c->NM, cudaMemcpyHostToDevice));
+    return BFS_OK;
+}
+
 int bfs_set_froude(bfs_ctx *c, double F)
 {
     if (!c) return BFS_EINVAL;
@@ -241,7 +264,7 @@ int bfs_check_finite(bfs_ctx *c, void *stream)
     BFS_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-    if (flag & 2) return set_err(c, BFS_ETIMEOUT, "a grid barrier of the preconditioner apply timed out");
+    if (flag & 2) return set_err(c, BFS_ETIMEOUT, "a wait in the preconditioner sweeps timed out");
     if (flag) return set_err(c, BFS_ENAN, "a residual entry was not finite");
     return BFS_OK;
 }

@@ -78,6 +78,7 @@ struct bfs_ctx {
     float *d_tgt32;                // Nt * TREC
     double *d_part;                // max splits * NACC * Nt
     double *d_constB;              // Nt: bottom-only single-layer part at bottom targets
+    double *d_psurf;               // NM applied surface pressure, or nullptr
     int *d_flag;                   // non-finite flag
     float *d_srcdf;                // Ns_cap * 32 double-float source records
     float *d_tgtdf;                // Nt * 32 double-float target records
@@ -101,6 +102,11 @@ struct bfs_ctx {
     // preconditioner
     int pc_ready, pc_h, nb, apply_grid;
     double *d_pc;      // M * (2h+1) * nb * nb  block-banded factors
+    float *d_pc32;     // FP32 copy of d_pc (precond_precision FP32C)
+    unsigned long long *d_flow;  // tagged y and z of the FP32 sweeps, 2 M nb
+    unsigned int flow_tag;       // tag of the next sweep launch's first step
+    int ldp32;                   // padded row length of d_pc32
+    int flow_checked;
     double *d_gj;      // 2 * nb * 2nb  Gauss-Jordan ping-pong
     double *d_rowsum5; // Nt
     int *d_pivflag;
@@ -126,6 +132,10 @@ PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, 
 void plans_for(int Nt, int Ns, int splits_req, int sms, PairPlan *p64, PairPlan *p32);
 
 int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s);
+
+// apply.cu
+int precond_make_f32(bfs_ctx *c, cudaStream_t s);
+int apply_flow_launch(bfs_ctx *c, const double *r, double *z, cudaStream_t s);
 extern const BatchVariant kBatchVariants[];
 extern const int kNumBatchVariants;
 int batch_pairs_occupancy(int v, int *blocks_per_sm);

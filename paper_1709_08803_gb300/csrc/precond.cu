@@ -423,11 +423,13 @@ struct ApplyArgs {
 
 constexpr int AP_TPB = 1024;
 constexpr int AP_WARPS = AP_TPB / 32;
+constexpr int AP_NQ = 4;  // columns per lane and block row (a warp covers <= 128 columns)
 
-// One CTA per SM.  Rows of a slice are dealt out round-robin over the CTAs,
-// and within a CTA over groups of warps; the warps of a group split the
-// columns of every block of the row and add their partial dots in shared
-// memory.
+// One CTA per SM.  Rows of a slice are dealt out round-robin over the CTAs and
+// within a CTA over groups of warps; the warps of a group split the columns
+// of the row (at most 128 per warp, 4 per lane), and every lane first issues
+// the loads of two blocks at once, so a step costs about two memory latencies
+// rather than one per column chunk.  Partial dots meet in shared memory.
 __global__ void __launch_bounds__(AP_TPB, 1) k_apply_coop(ApplyArgs a)
 {
     __shared__ double red[AP_WARPS];
@@ -436,15 +438,14 @@ __global__ void __launch_bounds__(AP_TPB, 1) k_apply_coop(ApplyArgs a)
     const int n = 3 * NB * M;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rpc = (nb + gridDim.x - 1) / gridDim.x;          // rows per CTA
-    const int groups = min(rpc, AP_WARPS);                      // warp groups
-    const int wpg = AP_WARPS / groups;                          // warps per group
+    const int rpc = (nb + gridDim.x - 1) / gridDim.x;                   // rows per CTA
+    const int wpg = min(AP_WARPS, (nb + 32 * AP_NQ - 1) / (32 * AP_NQ)); // warps per row
+    const int groups = AP_WARPS / wpg;                                   // rows per round
     const int grp = warp / wpg, wig = warp - grp * wpg;
     const int cw = (nb + wpg - 1) / wpg;
     const int c0 = wig * cw, c1 = min(nb, c0 + cw);
     unsigned int *cnt = &a.bar->count;
     unsigned int epoch = 0;
-    // rows of block row k that this warp reads, for the prefetch of the next step
     auto prefetch_step = [&](int pass, int k) {
         if (k < 0 || k >= M) return;
         int lo2, hi2;
@@ -472,32 +473,44 @@ __global__ void __launch_bounds__(AP_TPB, 1) k_apply_coop(ApplyArgs a)
     for (int pass = 0; pass < 2; pass++) {
         for (int kk = 0; kk < M; kk++) {
             const int k = pass == 0 ? kk : M - 1 - kk;
-            // the factor rows two steps ahead do not depend on this step: start
-            // bringing them into L2 now
             {
                 const int k2 = pass == 0 ? k + 2 : k - 2;
                 if (k2 >= 0 && k2 < M) prefetch_step(pass, k2);
                 else if (pass == 0) prefetch_step(1, M - 1 - (k2 - M));
             }
-            // blocks of this block row that enter the sweep
             int lo, hi;
             if (pass == 0) { lo = max(0, k - h); hi = k - 1; }   // L_ki, i < k, against y_i
             else { lo = k; hi = min(M - 1, k + h); }             // D_k^-1 y_k, W_kj x_j
-            // the trip count is the same for every thread of the CTA (the
-            // loop body has barriers); threads without a row compute nothing
+            // same trip count for every thread of the CTA (the body has barriers)
             for (int rb = 0; rb < rpc; rb += groups) {
                 const int rr = rb + grp;
                 const int row = (grp < groups && rr < rpc) ? blockIdx.x + rr * gridDim.x : nb;
                 double acc = 0.0;
                 if (row < nb) {
-                    for (int m = lo; m <= hi; m++) {
-                        const double *rp = a.pc + ((size_t)k * nd + (m - k + h)) * bsz + (size_t)row * nb;
-                        const double *v = (pass == 0 || m == k) ? a.y + (size_t)m * nb : a.x + (size_t)m * nb;
-                        const double sg = (pass == 1 && m == k) ? 1.0 : -1.0;
-                        double t = 0.0;
-#pragma unroll 4
-                        for (int c = c0 + lane; c < c1; c += 32) t = fma(__ldg(rp + c), __ldcg(v + c), t);
-                        acc = fma(sg, t, acc);
+                    for (int m = lo; m <= hi; m += 2) {
+                        double fa[2][AP_NQ], va[2][AP_NQ];
+#pragma unroll
+                        for (int bb = 0; bb < 2; bb++) {
+                            const int mm = m + bb;
+                            const bool ok = mm <= hi;
+                            const double *rp = a.pc + ((size_t)k * nd + (mm - k + h)) * bsz + (size_t)row * nb;
+                            const double *v = (pass == 0 || mm == k) ? a.y + (size_t)mm * nb : a.x + (size_t)mm * nb;
+#pragma unroll
+                            for (int q = 0; q < AP_NQ; q++) {
+                                const int c = c0 + lane + 32 * q;
+                                const bool in = ok && c < c1;
+                                fa[bb][q] = in ? __ldg(rp + c) : 0.0;
+                                va[bb][q] = in ? __ldcg(v + c) : 0.0;
+                            }
+                        }
+#pragma unroll
+                        for (int bb = 0; bb < 2; bb++) {
+                            const double sg = (pass == 1 && m + bb == k) ? 1.0 : -1.0;
+                            double t = 0.0;
+#pragma unroll
+                            for (int q = 0; q < AP_NQ; q++) t = fma(fa[bb][q], va[bb][q], t);
+                            acc = fma(sg, t, acc);
+                        }
                     }
                 }
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -534,6 +547,10 @@ static PcArgs pc_args(const bfs_ctx *c, int h)
 void precond_free(bfs_ctx *c)
 {
     cudaFree(c->d_pc);
+    cudaFree(c->d_pc32);
+    cudaFree(c->d_flow);
+    c->d_pc32 = nullptr;
+    c->d_flow = nullptr;
     cudaFree(c->d_gj);
     cudaFree(c->d_rowsum5);
     cudaFree(c->d_pivflag);
@@ -636,6 +653,12 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
         c->err = "zero pivot in a diagonal block of the preconditioner";
         return BFS_ESINGULAR;
     }
+    if (c->opt.precond_precision == BFS_FP32C) {
+        int rc = precond_make_f32(c, s);
+        if (rc) return rc;
+        BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
+    c->flow_checked = 0;
     c->pc_ready = 1;
     return BFS_OK;
 }
@@ -645,6 +668,19 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
     if (!c->pc_ready) {
         c->err = "preconditioner applied before bfs_precond_factor";
         return BFS_ENOPREC;
+    }
+    cudaEvent_t ev1 = nullptr;
+    if (c->prof_on) {
+        cudaEvent_t ev0 = prof_event(c);
+        ev1 = prof_event(c);
+        c->ev_kind.push_back(3);
+        cudaEventRecord(ev0, s);
+    }
+    const int split = apply_flow_launch(c, r, z, s);
+    if (split < 0) return split;
+    if (split == 1) {
+        if (ev1) cudaEventRecord(ev1, s);
+        return BFS_OK;
     }
     if (c->apply_grid <= 0) {
         int per_sm = 0;
@@ -661,13 +697,6 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
     a.bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
     a.flag = c->d_flag;
     BFS_CUDA_TRY(c, cudaMemsetAsync(a.bar, 0, sizeof(CoopBar), s));
-    cudaEvent_t ev1 = nullptr;
-    if (c->prof_on) {
-        cudaEvent_t ev0 = prof_event(c);
-        ev1 = prof_event(c);
-        c->ev_kind.push_back(3);
-        cudaEventRecord(ev0, s);
-    }
     void *args[] = {&a};
     BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_apply_coop, dim3(c->apply_grid),
                                                 dim3(AP_TPB), args, 0, s));

@@ -341,7 +341,8 @@ struct FinArgs {
 // lanes), radiation rows per slice.
 __global__ void k_finish(const double *__restrict__ part, const double *__restrict__ tgt,
                          const double *__restrict__ constB, const double *__restrict__ nodal,
-                         double *__restrict__ Fu, int *__restrict__ flag, FinArgs a)
+                         const double *__restrict__ psurf, double *__restrict__ Fu,
+                         int *__restrict__ flag, FinArgs a)
 {
     const double TWO_PI = 6.283185307179586476925286766559;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -381,7 +382,11 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
         const double F7 = acc[3] + acc[4] + constB[e] - TWO_PI * gs;
         const double num = (1.0 + zxs * zxs) * pys * pys + (1.0 + zys * zys) * pxs * pxs -
                            2.0 * zxs * zys * pxs * pys;
-        const double F1 = 0.5 * num / (1.0 + zxs * zxs + zys * zys) + zs / (a.F * a.F) - 0.5;
+        double F1 = 0.5 * num / (1.0 + zxs * zxs + zys * zys) + zs / (a.F * a.F) - 0.5;
+        if (psurf) {  // applied surface pressure at the half point (Sec. 4.1)
+            const size_t qa = (size_t)l * N + k;
+            F1 += 0.5 * (psurf[qa] + psurf[qa + 1]);
+        }
         const size_t row = (size_t)l * (N + 1) + 2 + k;
         Fu[row] = F1;
         Fu[blk + row] = F2;
@@ -522,7 +527,7 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
     if (ev1) cudaEventRecord(ev1, s);
     FinArgs fa = fin_args(c, p.splits);
     int tot = 4 * (c->Nt + c->M);
-    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, Fu,
+    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
                                                c->d_flag, fa);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());
@@ -534,7 +539,7 @@ int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s)
     const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
     FinArgs fa = fin_args(c, p.splits);
     int tot = 4 * (c->Nt + c->M);
-    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, Fu,
+    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
                                                c->d_flag, fa);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());

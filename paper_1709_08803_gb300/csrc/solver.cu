@@ -510,7 +510,7 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             BFS_CUDA_TRY(c, cudaMemcpyAsync(&fl, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
             BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
             if (fl & 2) {
-                c->err = "a grid barrier of the preconditioner apply timed out";
+                c->err = "a wait in the preconditioner sweeps timed out";
                 return finish(BFS_ETIMEOUT);
             }
         }

@@ -132,9 +132,66 @@ def test_precond_apply_matches_dense_solve(name, half_band):
     r = np.random.default_rng(11).standard_normal(mesh.n_unknowns)
     ref = np.linalg.solve(Jb, r)
     got = ctx.precond_apply(_dev(r)).cpu().numpy()
+    assert ctx.check_finite()
     assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
     # P z = r holds to rounding
     assert np.abs(Jb @ got - r).max() <= 1e-9 * np.abs(r).max() * np.abs(Jb).max()
+
+
+# Meshes whose slice block (3(N+1) rows) spreads over more than 4 rows per SM
+# (the wider register tiles of the sweep kernel) and one beyond them (the
+# fallback sweep kernel).
+WIDE = {
+    "wide_241x3": W.mesh_box(241, 3, 0.4, 0.4),
+    "wide_361x3": W.mesh_box(361, 3, 0.4, 0.4),
+    "wide_409x3": W.mesh_box(409, 3, 0.4, 0.4),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WIDE))
+def test_precond_apply_wide_slices(name):
+    mesh = WIDE[name]
+    ctx = _ctx(mesh, W.flat_topography(mesh), 0.7)
+    ctx.precond_factor(1)
+    Jb = O.jtilde(O.problem(mesh, 0.7), half_band=1)
+    r = np.random.default_rng(12).standard_normal(mesh.n_unknowns)
+    got = ctx.precond_apply(_dev(r)).cpu().numpy()
+    assert ctx.check_finite()
+    # backward error of an FP64 solve (these blocks are ill-conditioned, so
+    # the forward error is not a rounding-level quantity)
+    assert np.abs(Jb @ got - r).max() <= 1e-9 * np.abs(r).max() * np.abs(Jb).max()
+
+
+@pytest.mark.parametrize("half_band", [1, 3])
+@pytest.mark.parametrize("name", ["ragged_full_23x9", "small_half_31x11", "wide_241x3", "wide_361x3"])
+def test_precond_apply_fp32(name, half_band):
+    """FP32 sweeps over an FP32 copy of the FP64 factors.
+
+    Well-conditioned meshes (cond ~1e4): the backward error stays within the
+    probabilistic rounding bound 4 sqrt(n) u32 (|P| |z|)_max of a length-n
+    sum (Higham and Mary, SIAM J. Sci. Comput. 41, 2019), n = nd nb the
+    entries one row sums, u32 = 2^-24.  Wide meshes (cond ~1e7-1e8, where any
+    FP32 solve loses most digits): P z must still be within 5 % of r, i.e. the
+    FP32 operator keeps the preconditioned spectrum clustered at 1 that the
+    preconditioner exists for (Sec. 4.2)."""
+    from paper_1709_08803_gb300 import bfs
+    mesh = WIDE.get(name) or MESHES[name][0]
+    F = MESHES[name][1] if name in MESHES else 0.7
+    hb = min(half_band, mesh.M - 1)
+    ctx = _ctx(mesh, W.flat_topography(mesh), F, precond_precision=bfs.BFS_FP32C)
+    ctx.precond_factor(hb)
+    Jb = O.jtilde(O.problem(mesh, F), half_band=hb)
+    r = np.random.default_rng(13).standard_normal(mesh.n_unknowns)
+    got = ctx.precond_apply(_dev(r)).cpu().numpy()
+    assert ctx.check_finite()  # raises BfsError(BFS_ETIMEOUT) if a sweep wait gave up
+    res = np.abs(Jb @ got - r).max()
+    if name in WIDE:
+        assert res <= 0.05 * np.abs(r).max(), res
+    else:
+        n = (2 * hb + 1) * 3 * (mesh.N + 1)
+        u32 = 2.0 ** -24
+        bound = 4.0 * math.sqrt(n) * u32 * (np.abs(Jb) @ np.abs(got)).max() + u32 * np.abs(r).max()
+        assert res <= bound, (res, bound)
 
 
 def test_precond_apply_before_factor_is_an_error():
@@ -276,3 +333,63 @@ def test_set_topography_and_froude_keep_the_preconditioner():
     assert np.abs(O.residual(O.problem(mesh, 0.75), bigger, u.cpu().numpy())).max() <= 1e-10
     with pytest.raises(bfs.BfsError):
         ctx.set_froude(0.0)
+
+
+@pytest.mark.parametrize("name", ["small_half_31x11", "ragged_full_23x9"])
+def test_bottom_pressure_matches_oracle(name):
+    mesh, F = MESHES[name]
+    topo = _topo(mesh)
+    ctx = _ctx(mesh, topo, F)
+    u = W.smooth_guess(mesh, 6)
+    pr, fr = O.bottom_pressure(O.problem(mesh, F), topo, u)
+    p, f = ctx.bottom_pressure(_dev(u))
+    assert np.abs(p.cpu().numpy() - pr).max() <= 1e-12 * max(1.0, np.abs(pr).max())
+    assert np.abs(f - fr).max() <= 1e-10 * max(1.0, np.abs(fr).max())
+
+
+def test_surface_pressure_residual_and_solve():
+    """The pressure-distribution problem (flat bottom, applied surface pressure):
+    residual parity with the oracle and a converged solve it accepts."""
+    from oracle import linear_fft as LF
+    mesh, topo, F = W.config_small_half()
+    flat = W.flat_topography(mesh)
+    p = LF.equivalent_pressure(lambda X, Y: 0.1 * np.exp(-(X * X + Y * Y)), F, mesh.x(), mesh.y())
+    ctx = _ctx(mesh, flat, F, tol=1e-10)
+    ctx.set_surface_pressure(p)
+    P = O.problem(mesh, F, psurf=p)
+    u = W.smooth_guess(mesh, 8)
+    ref, sc = O.residual(P, flat, u, with_scale=True)
+    got = ctx.residual(_dev(u)).cpu().numpy()
+    assert np.all(np.abs(got - ref) <= TOL64 * sc + 1e-13)
+    u0 = ctx.flat_guess()
+    assert ctx.solve(u0)["status"] == 0
+    assert np.abs(O.residual(P, flat, u0.cpu().numpy())).max() <= 1e-10
+    ctx.set_surface_pressure(None)
+    assert np.abs(ctx.residual(u0).cpu().numpy()).max() > 1e-6  # the forcing is gone
+
+
+# ---------------------------------------------------------------------------
+# 361 x 121 (about 87 000 collocation points, 7.6e9 pair evaluations per
+# residual): FP64 and double-float residuals against the full oracle residual,
+# and the FP32C error, at a wave-like state.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def large_case():
+    mesh, topo, F = W.config_large()
+    P = O.problem(mesh, F)
+    u = W.smooth_guess(mesh, 9)
+    ref, sc = O.residual(P, topo, u, with_scale=True)
+    return mesh, topo, F, u, ref, sc
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32c"])
+def test_large_config_residual(large_case, prec):
+    from paper_1709_08803_gb300 import bfs
+    mesh, topo, F, u, ref, sc = large_case
+    ctx = _ctx(mesh, topo, F)
+    pr = {"fp64": bfs.BFS_FP64, "df64": bfs.BFS_DF64, "fp32c": bfs.BFS_FP32C}[prec]
+    got = ctx.residual(_dev(u), precision=pr).cpu().numpy()
+    rel = np.abs(got - ref) / (sc + 1e-300)
+    print(f"361x121 {prec}: max |dF|/scale = {rel.max():.3e}")
+    assert rel.max() <= (TOL32 if prec == "fp32c" else TOL64)
+    ctx.close()
