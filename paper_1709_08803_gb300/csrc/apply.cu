@@ -306,50 +306,33 @@ __device__ __forceinline__ void compute_sync(int ct)
 template <int CT, int RPC, int CPT, int BMAX>
 __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
 {
+    // Block positions of a step (slot layout): forward step k multiplies
+    // L_k,k-p at position p = 1..h (p = 1 is the dependent one); backward
+    // step k multiplies D_k^-1 at p = 0 and W_k,k+p at p = 1..h (p = 1
+    // dependent; at k = M-1 the D^-1 term is the dependent one).
     constexpr int WARPS = CT / 32;
     constexpr int MAXSLOT = 8;
+    constexpr int HW = BMAX - 2 > 0 ? BMAX - 2 : 1;  // vectors kept from earlier steps
     extern __shared__ __align__(128) float ring[];  // nslot x BMAX x RPC x ldp
     __shared__ __align__(8) unsigned long long full[MAXSLOT], empty[MAXSLOT];
-    __shared__ float red[RPC][WARPS];
+    __shared__ float red[2][RPC][WARPS];
     const float *pc = a.pc;
-    const int nb = a.nb, NB = a.NB, M = a.M, h = a.h, nd = 2 * h + 1, G = gridDim.x, ldp = a.ldp;
-    const int nslot = a.nslot;
+    const int nb = a.nb, NB = a.NB, M = a.M, h = a.h, nd = 2 * h + 1, ldp = a.ldp;
+    const int nslot = a.nslot, G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t slot_floats = (size_t)BMAX * RPC * ldp;
     // rows [r0, r0 + nrv): the first nb % G CTAs take one row more
     const int base = nb / G, extra = nb % G;
     const int nrv = base + (blockIdx.x < extra ? 1 : 0);
     const int r0 = blockIdx.x * base + min((int)blockIdx.x, extra);
-
-    auto terms_of = [&](int s, int (&mt)[BMAX], int &nt, int &cs, int &pass, int &k) {
-        pass = s < M ? 0 : 1;
-        k = pass == 0 ? s : 2 * M - 1 - s;
-        int lo, hi, crit;
-        if (pass == 0) {
-            lo = max(0, k - h); hi = k - 1;
-            crit = (k >= 1 && h >= 1) ? k - 1 : -1;
-        } else {
-            lo = k; hi = min(M - 1, k + h);
-            crit = (k == M - 1) ? k : (h >= 1 ? k + 1 : -1);
+    // block column m at position p of step s (-1: no block there)
+    auto pos_m = [&](int s, int p) {
+        if (s < M) {
+            const int k = s, m = k - p;
+            return (p >= 1 && p <= h && m >= 0) ? m : -1;
         }
-        nt = 0;
-#pragma unroll
-        for (int t = 0; t < BMAX; t++) mt[t] = k;
-        for (int m = lo; m <= hi; m++)
-            if (m != crit) {
-#pragma unroll
-                for (int t = 0; t < BMAX; t++)
-                    if (t == nt) mt[t] = m;
-                nt++;
-            }
-        cs = -1;
-        if (crit >= 0) {
-#pragma unroll
-            for (int t = 0; t < BMAX; t++)
-                if (t == nt) mt[t] = crit;
-            cs = nt;
-            nt++;
-        }
+        const int k = 2 * M - 1 - s, m = k + p;
+        return (p <= h && m <= M - 1) ? m : -1;
     };
 
     if (tid == 0) {
@@ -362,42 +345,50 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
     __syncthreads();
 
     if (warp == WARPS) {
-        // producer warp: one lane issues; slot of step q is q % nslot
-        if (lane == 0) {
-            int q = 0;
-            bool fine = true;
-            for (; q < 2 * M; q++) {
-                const int slot = q % nslot;
-                if (q >= nslot && !mbar_wait(smem_u32(&empty[slot]), (unsigned int)((q / nslot - 1) & 1))) {
-                    atomicOr(a.flag, 2);
+        // producer warp: lane L copies row L % RPC of position L / RPC
+        const int p = lane / RPC, j = lane % RPC;
+        int q = 0;
+        bool fine = true;
+        for (; q < 2 * M; q++) {
+            const int slot = q % nslot;
+            if (q >= nslot) {
+                int w = 1;
+                if (lane == 0) w = mbar_wait(smem_u32(&empty[slot]), (unsigned int)((q / nslot - 1) & 1)) ? 1 : 0;
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) {
+                    if (lane == 0) atomicOr(a.flag, 2);
                     fine = false;
                     break;
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                int mt[BMAX], nt, cs, pass, k;
-                terms_of(q, mt, nt, cs, pass, k);
-                const unsigned int fb = smem_u32(&full[slot]);
-                const unsigned int span = (unsigned int)(nrv * ldp * 4);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(span * nt)
-                             : "memory");
-                if (span == 0) continue;
-                float *dst = ring + (size_t)slot * slot_floats;
-#pragma unroll
-                for (int t = 0; t < BMAX; t++) {
-                    if (t < nt) {
-                        const float *src = pc + (((size_t)k * nd + (mt[t] - k + h)) * nb + r0) * ldp;
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                smem_u32(dst + (size_t)t * RPC * ldp)),
-                            "l"(src), "r"(span), "r"(fb)
-                            : "memory");
-                    }
-                }
             }
-            // every copy issued must land before the CTA may end
+            const int k = q < M ? q : 2 * M - 1 - q;
+            int npos = 0;
+            for (int pp = 0; pp < BMAX; pp++) npos += pos_m(q, pp) >= 0 ? 1 : 0;
+            const unsigned int fb = smem_u32(&full[slot]);
+            const unsigned int row_bytes = (unsigned int)(ldp * 4);
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                             "r"(row_bytes * (unsigned int)(npos * nrv))
+                             : "memory");
+            }
+            __syncwarp();
+            const int m = p < BMAX ? pos_m(q, p) : -1;
+            if (m >= 0 && j < nrv) {
+                const float *src = pc + (((size_t)k * nd + (m - k + h)) * nb + r0 + j) * ldp;
+                float *dst = ring + (size_t)slot * slot_floats + ((size_t)p * RPC + j) * ldp;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(dst)),
+                    "l"(src), "r"(row_bytes), "r"(fb)
+                    : "memory");
+            }
+        }
+        // every copy issued must land before the CTA may end
+        if (lane == 0) {
             const int last = fine ? 2 * M - 1 : q - 1;
-            for (int p = max(0, last - nslot + 1); p <= last; p++)
-                if (!mbar_wait(smem_u32(&full[p % nslot]), (unsigned int)((p / nslot) & 1))) break;
+            for (int pq = max(0, last - nslot + 1); pq <= last; pq++)
+                if (!mbar_wait(smem_u32(&full[pq % nslot]), (unsigned int)((pq / nslot) & 1))) break;
         }
         return;
     }
@@ -414,34 +405,32 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
     const int my_j = tid < nrv ? tid : -1;
     size_t my_e = 0;
     if (my_j >= 0) {
-        const int rw = r0 + my_j, g = rw / NB, p = rw - g * NB;
-        my_e = (size_t)g * NB * M + p;
+        const int rw = r0 + my_j, g = rw / NB, pp = rw - g * NB;
+        my_e = (size_t)g * NB * M + pp;
     }
-    auto producer = [&](int pass, int k, int m) { return (pass == 0 || m == k) ? m : 2 * M - 1 - m; };
-    auto vec = [&](int pass, int k, int m) -> const unsigned long long * {
-        return (pass == 0 || m == k) ? a.Y + (size_t)m * nb : a.X + (size_t)m * nb;
-    };
-    unsigned long long Vw[BMAX][CPT];
+    float win[HW][CPT];  // forward: y_{k-2-i}; backward: z_{k+2+i} (this thread's columns)
+    unsigned long long yw[CPT];  // backward: the word of y_k, loaded one step early
 #pragma unroll
-    for (int t = 0; t < BMAX; t++)
+    for (int q = 0; q < CPT; q++) {
+        yw[q] = 0ull;
 #pragma unroll
-        for (int q = 0; q < CPT; q++) Vw[t][q] = 0ull;
-    auto load_vecs = [&](int s) {
-        int mt[BMAX], nt = 0, cs = -1, pass = 0, k = 0;
-        if (s < 2 * M) terms_of(s, mt, nt, cs, pass, k);
+        for (int i = 0; i < HW; i++) win[i][q] = 0.f;
+    }
+    auto dot = [&](const float *S, int p, const float (&v)[CPT], float (&acc)[RPC], float sg) {
 #pragma unroll
-        for (int t = 0; t < BMAX; t++) {
-            const bool ut = t < nt && t != cs;
-            const unsigned long long *vp = vec(pass, k, ut ? mt[t] : k);
+        for (int j = 0; j < RPC; j++) {
+            float u = 0.f;
 #pragma unroll
-            for (int q = 0; q < CPT; q++) Vw[t][q] = (ut && cv[q]) ? ld_word(vp + col[q]) : 0ull;
+            for (int q = 0; q < CPT; q++)
+                if (cv[q] && j < nrv) u = fmaf(S[((size_t)p * RPC + j) * ldp + col[q]], v[q], u);
+            acc[j] = fmaf(sg, u, acc[j]);
         }
     };
 
     bool ok = true;
     for (int s = 0; s < 2 * M; s++) {
-        int mt[BMAX], nt, cs, pass, k;
-        terms_of(s, mt, nt, cs, pass, k);
+        const int pass = s < M ? 0 : 1;
+        const int k = pass == 0 ? s : 2 * M - 1 - s;
         double xk = 0.0;
         if (pass == 0 && my_j >= 0) xk = a.r[my_e + (size_t)k * NB];
         const int slot = s % nslot;
@@ -450,59 +439,59 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
         float acc[RPC];
 #pragma unroll
         for (int j = 0; j < RPC; j++) acc[j] = 0.f;
+        // terms whose vectors this thread already holds
 #pragma unroll
-        for (int t = 0; t < BMAX; t++) {
-            if (ok && t < nt && t != cs) {
-                const unsigned int tg = a.tag0 + producer(pass, k, mt[t]);
-                const unsigned long long *vp = vec(pass, k, mt[t]);
-                const float sg = (pass == 1 && mt[t] == k) ? 1.f : -1.f;
-                float v[CPT];
+        for (int p = 2; p < BMAX; p++)
+            if (ok && pos_m(s, p) >= 0) dot(S, p, win[p - 2], acc, -1.f);
+        if (ok && pass == 1 && k < M - 1) {
+            float v[CPT];
+#pragma unroll
+            for (int q = 0; q < CPT; q++) {
+                v[q] = 0.f;
+                if (cv[q]) {
+                    if ((unsigned int)(yw[q] >> 32) == a.tag0 + (unsigned int)k) v[q] = __uint_as_float((unsigned int)yw[q]);
+                    else if (ok) ok = await_word(a.Y + (size_t)k * nb + col[q], a.tag0 + (unsigned int)k, v[q]);
+                }
+            }
+            dot(S, 0, v, acc, 1.f);
+        }
+        // the dependent term: the vector finished by step s-1
+        const bool turn = pass == 1 && k == M - 1;
+        if (ok && (turn || pos_m(s, 1) >= 0)) {
+            const unsigned long long *vp = turn ? a.Y + (size_t)k * nb
+                                                : (pass == 0 ? a.Y + (size_t)(k - 1) * nb : a.X + (size_t)(k + 1) * nb);
+            const unsigned int tg = a.tag0 + (unsigned int)(s - 1);
+            float v[CPT];
+#pragma unroll
+            for (int q = 0; q < CPT; q++) {
+                v[q] = 0.f;
+                if (ok && cv[q]) ok = await_word(vp + col[q], tg, v[q]);
+            }
+            if (turn) {
+                dot(S, 0, v, acc, 1.f);
+            } else {
+                dot(S, 1, v, acc, -1.f);
 #pragma unroll
                 for (int q = 0; q < CPT; q++) {
-                    v[q] = 0.f;
-                    if (cv[q]) {
-                        if ((unsigned int)(Vw[t][q] >> 32) == tg) v[q] = __uint_as_float((unsigned int)Vw[t][q]);
-                        else if (ok) ok = await_word(vp + col[q], tg, v[q]);
-                    }
-                }
 #pragma unroll
-                for (int j = 0; j < RPC; j++) {
-                    float u = 0.f;
-#pragma unroll
-                    for (int q = 0; q < CPT; q++)
-                        if (cv[q] && j < nrv) u = fmaf(S[((size_t)t * RPC + j) * ldp + col[q]], v[q], u);
-                    acc[j] = fmaf(sg, u, acc[j]);
+                    for (int i = HW - 1; i > 0; i--) win[i][q] = win[i - 1][q];
+                    win[0][q] = v[q];
                 }
             }
         }
+        if (turn) {  // the backward window starts empty
 #pragma unroll
-        for (int t = 0; t < BMAX; t++) {
-            if (ok && t == cs) {
-                const unsigned int tg = a.tag0 + (unsigned int)(s - 1);
-                const unsigned long long *vp = vec(pass, k, mt[t]);
-                const float sg = (pass == 1 && mt[t] == k) ? 1.f : -1.f;
-                float v[CPT];
+            for (int q = 0; q < CPT; q++)
 #pragma unroll
-                for (int q = 0; q < CPT; q++) {
-                    v[q] = 0.f;
-                    if (ok && cv[q]) ok = await_word(vp + col[q], tg, v[q]);
-                }
-#pragma unroll
-                for (int j = 0; j < RPC; j++) {
-                    float u = 0.f;
-#pragma unroll
-                    for (int q = 0; q < CPT; q++)
-                        if (cv[q] && j < nrv) u = fmaf(S[((size_t)t * RPC + j) * ldp + col[q]], v[q], u);
-                    acc[j] = fmaf(sg, u, acc[j]);
-                }
-            }
+                for (int i = 0; i < HW; i++) win[i][q] = 0.f;
         }
+        float(&rd)[RPC][WARPS] = red[s & 1];
 #pragma unroll
         for (int j = 0; j < RPC; j++) {
             float u = acc[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            if (lane == 0) red[j][warp] = u;
+            if (lane == 0) rd[j][warp] = u;
         }
         if (!compute_sync_and(ok, CT)) {
             if (tid == 0) atomicOr(a.flag, 2);
@@ -513,7 +502,7 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
         if (my_j >= 0) {
             float u = 0.f;
 #pragma unroll
-            for (int w = 0; w < WARPS; w++) u += red[my_j][w];
+            for (int w = 0; w < WARPS; w++) u += rd[my_j][w];
             const size_t si = (size_t)k * nb + r0 + my_j;
             const unsigned int tg = a.tag0 + (unsigned int)s;
             if (pass == 0) {
@@ -523,8 +512,14 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
                 a.z[my_e + (size_t)k * NB] = (double)u;
             }
         }
-        load_vecs(s + 1);
-        compute_sync(CT);  // red is rewritten by the next step
+        // y_k of the next backward step (finished long before)
+        if (s + 1 > M && s + 1 < 2 * M) {
+            const int kn = 2 * M - 2 - s;
+#pragma unroll
+            for (int q = 0; q < CPT; q++) yw[q] = cv[q] ? ld_word(a.Y + (size_t)kn * nb + col[q]) : 0ull;
+        }
+        // red[s & 1] is next written at step s + 2, after every thread has
+        // passed the barrier of step s + 1
     }
 }
 
@@ -588,7 +583,7 @@ int apply_flow_launch(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
     const int rpc = (c->nb + G - 1) / G, cpt = (c->nb + FL_TPB - 1) / FL_TPB;
     const size_t slot_bytes = (size_t)TMA_BMAX * TMA_RPC * c->ldp32 * sizeof(float);
     int nslot = (int)std::min<size_t>(TMA_MAXSLOT, TMA_SMEM_MAX / slot_bytes);
-    nslot = std::min(nslot, 4);
+    nslot = std::min(nslot, 6);
     const bool tma = rpc <= TMA_RPC && c->nb <= TMA_CT * TMA_CPT && c->pc_h < TMA_BMAX && nslot >= 2;
     FlowKernel kern = tma ? k_apply_tma<TMA_CT, TMA_RPC, TMA_CPT, TMA_BMAX> : pick_flow(rpc, cpt);
     const int tpb = tma ? TMA_CT + 32 : FL_TPB;
