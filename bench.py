@@ -211,7 +211,7 @@ def run_batch(args):
     meshes, topos, Fs = W.config_batch(seed=3, B=args.batch)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=args.eta, max_newton=30, max_krylov=150, time_budget_s=60.0,
-                               precond_precision=_pc_prec(args))
+                               precond_precision=_pc_prec(args), refine_below=args.refine_below)
     t0 = time.perf_counter()
     b = bfs.Batch(meshes, topos, Fs, opts)
     setup_s = time.perf_counter() - t0
@@ -280,6 +280,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--F", type=float, default=0.7)
     ap.add_argument("--eta", type=float, default=1e-2)
+    ap.add_argument("--refine-below", type=float, default=1e-5,
+                    help="mixed form: FP32C Newton residuals while |F|inf exceeds this, DF64 after (0: DF64 throughout)")
     ap.add_argument("--precond", default="fp32", choices=["fp32", "fp64"],
                     help="storage/arithmetic of the preconditioner sweeps in the mixed form")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
@@ -314,7 +316,8 @@ def main():
 
     mesh, topo, F = W.config_paper_scale(args.F)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=args.eta, precond_precision=_pc_prec(args))
+                               eta=args.eta, precond_precision=_pc_prec(args),
+                               refine_below=args.refine_below)
     ctx = bfs.Context(mesh, topo, F, opts)
     pairs_per_residual = ctx.pair_evals
     n_index_pairs = mesh.n_targets * mesh.n_sources
@@ -457,8 +460,10 @@ def main():
                                        "solve from the uniform stream to |F|inf<=1e-8" % F,
                            "form": "mixed: FP32C residuals inside Jv; Newton residual and line search in "
                                    "double-float (FP64-accurate, 1e-10 per-row parity); FP64 GMRES and "
-                                   "banded-LU factorisation; preconditioner sweeps in %s; no learned "
-                                   "guess" % ("FP32 over FP32 copies of the factors" if args.precond == "fp32" else "FP64"),
+                                   "banded-LU factorisation; preconditioner sweeps in %s; Newton residuals in "
+                                   "FP32C while |F|inf > %g, double-float after; no learned guess" % (
+                                       "FP32 over FP32 copies of the factors" if args.precond == "fp32" else "FP64",
+                                       args.refine_below),
                            "l2": "flushed between steps (256 MiB write); sources fit in L2",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "precond_half_band": int(opts.half_band if opts.half_band > 0 else max(1, round(mesh.M / 20))),

@@ -99,6 +99,12 @@ typedef struct {
                               either way; FP32C sweeps an FP32 copy of the factors
                               (the preconditioner only steers GMRES, the Newton
                               residual and the converged u do not depend on it) */
+    double refine_below;   /* > 0 with outer_precision != krylov_precision: the Newton
+                              residual and the line search use the Krylov arithmetic
+                              while |F|_inf > refine_below, then switch to
+                              outer_precision for the final steps (iterative
+                              refinement); convergence is only ever accepted on an
+                              outer_precision residual.  0 (default): always outer. */
 } bfs_options;
 
 typedef struct {

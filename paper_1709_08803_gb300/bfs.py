@@ -50,7 +50,8 @@ class bfs_options(ctypes.Structure):
                 ("max_krylov", ctypes.c_int), ("eta", ctypes.c_double),
                 ("krylov_precision", ctypes.c_int), ("jv_h_rel", ctypes.c_double),
                 ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
-                ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int)]
+                ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int),
+                ("refine_below", ctypes.c_double)]
 
 
 class bfs_stats(ctypes.Structure):

@@ -85,6 +85,7 @@ void bfs_default_options(bfs_options *o)
     o->src_splits = 0;
     o->outer_precision = BFS_FP64;
     o->precond_precision = BFS_FP64;
+    o->refine_below = 0.0;
 }
 
 const char *bfs_last_error(const bfs_ctx *c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -119,6 +120,7 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
         return set_err(nullptr, BFS_EINVAL, "sign_I4 must be +1 or -1");
     if (o.krylov_precision != BFS_FP64 && o.krylov_precision != BFS_FP32C && o.krylov_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "unknown krylov_precision");
+    if (!(o.refine_below >= 0.0)) return set_err(nullptr, BFS_EINVAL, "refine_below must be >= 0");
     if (o.precond_precision != BFS_FP64 && o.precond_precision != BFS_FP32C)
         return set_err(nullptr, BFS_EINVAL, "precond_precision must be BFS_FP64 or BFS_FP32C");
     if (o.outer_precision != BFS_FP64 && o.outer_precision != BFS_DF64)

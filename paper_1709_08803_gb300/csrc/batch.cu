@@ -333,8 +333,11 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
     }
     if (!b->g_up && (rc = capture_up_graph(b))) return rc;
     const bfs_options &o = b->c[0]->opt;
-    const bool need_base = o.krylov_precision != o.outer_precision;
     const bool k32 = o.krylov_precision == BFS_FP32C;
+    // per instance: arithmetic of the Newton residual (the Krylov one while
+    // |F| > refine_below, then the outer one)
+    const int outer = o.outer_precision;
+    std::vector<int> cur(B, (o.refine_below > 0.0 && o.krylov_precision != outer) ? o.krylov_precision : outer);
     std::vector<bfs_stats> S(B);
     std::vector<bfs::Gm> g(B);
     std::vector<int> status(B, 1);  // 1 running, else final status
@@ -347,8 +350,9 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
             bfs_ctx *c = b->c[i];
             const double *x = trial ? c->d_ut : u[i];
             double *y = trial ? c->d_Ft : c->d_F;
-            if ((rc = bfs::residual_launch(c, x, y, o.outer_precision, s))) return berr(b, rc, c->err);
-            S[i].residual_evals_fp64++;
+            if ((rc = bfs::residual_launch(c, x, y, cur[i], s))) return berr(b, rc, c->err);
+            if (cur[i] == BFS_FP32C) S[i].residual_evals_fp32++;
+            else S[i].residual_evals_fp64++;
             bfs::norms_launch(c, y, c->n, c->d_scal + 10, c->d_scal + 11, s);
         }
         return read_batch(b, who, 10, 2, s);
@@ -377,6 +381,20 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
     for (int i = 0; i < B; i++) { f2[i] = b->h_sc[4 * i]; finf[i] = b->h_sc[4 * i + 1]; }
 
     for (int k = 0;; k++) {
+        {
+            // instances close enough for the final arithmetic switch to it
+            std::vector<int> sw;
+            for (int i = 0; i < B; i++)
+                if (status[i] == 1 && cur[i] != outer && isfinite(finf[i]) &&
+                    (finf[i] <= o.refine_below || finf[i] <= o.tol)) {
+                    cur[i] = outer;
+                    sw.push_back(i);
+                }
+            if (!sw.empty()) {
+                if ((rc = outer_residuals(sw, false))) return rc;
+                for (int i : sw) { f2[i] = b->h_sc[4 * i]; finf[i] = b->h_sc[4 * i + 1]; }
+            }
+        }
         std::vector<int> act;
         for (int i = 0; i < B; i++) {
             if (status[i] != 1) continue;
@@ -392,18 +410,21 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
         }
         if (act.empty()) break;
         // base residuals of the finite differences, in the Krylov arithmetic
-        if (need_base) {
+        std::vector<int> base;
+        for (int i : act)
+            if (cur[i] != o.krylov_precision) base.push_back(i);
+        if (!base.empty()) {
             if (k32) {
                 std::vector<char> on(B, 0);
-                for (int i : act) on[i] = 1;
+                for (int i : base) on[i] = 1;
                 if ((rc = set_mask(b, on, s))) return rc;
                 std::vector<const double *> uu(B);
                 std::vector<double *> FF(B);
                 for (int i = 0; i < B; i++) { uu[i] = u[i]; FF[i] = b->c[i]->d_F32; }
                 if ((rc = batched_residual32(b, uu, FF, b->variant, b->grid, s))) return rc;
-                for (int i : act) S[i].residual_evals_fp32++;
+                for (int i : base) S[i].residual_evals_fp32++;
             } else {
-                for (int i : act) {
+                for (int i : base) {
                     bfs_ctx *c = b->c[i];
                     if ((rc = bfs::residual_launch(c, u[i], c->d_F32, o.krylov_precision, s))) return berr(b, rc, c->err);
                     S[i].residual_evals_fp64++;
@@ -416,7 +437,8 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
             gi.precs = g[i].precs;
             gi.jvs = g[i].jvs;
             g[i] = gi;
-            bfs::gm_start(c, g[i], u[i], c->d_F, need_base ? c->d_F32 : c->d_F, f2[i], o.eta, o.max_krylov, s);
+            bfs::gm_start(c, g[i], u[i], c->d_F, cur[i] != o.krylov_precision ? c->d_F32 : c->d_F, f2[i], o.eta,
+                          o.max_krylov, s);
         }
         if ((rc = read_batch(b, act, 8, 1, s))) return rc;
         for (int i : act) bfs::gm_cycle_begin(b->c[i], g[i], b->h_sc[4 * i], s);

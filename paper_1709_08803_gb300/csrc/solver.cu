@@ -474,12 +474,29 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         return status;
     };
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-    if ((rc = residual_launch(c, u, c->d_F, c->opt.outer_precision, s))) return finish(rc);
-    S.residual_evals_fp64++;
+    // arithmetic of the Newton residual and line search: the Krylov one while
+    // |F| is large (refine_below > 0), the outer one for the final steps
+    const int outer = c->opt.outer_precision;
+    int cur = (c->opt.refine_below > 0.0 && c->opt.krylov_precision != outer) ? c->opt.krylov_precision : outer;
+    auto count = [&](int prec) {
+        if (prec == BFS_FP32C) S.residual_evals_fp32++;
+        else S.residual_evals_fp64++;
+    };
+    if ((rc = residual_launch(c, u, c->d_F, cur, s))) return finish(rc);
+    count(cur);
     norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
     if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
     double f2 = c->h_pin[0], finf = c->h_pin[1];
     for (int k = 0;; k++) {
+        if (cur != outer && isfinite(finf) && (finf <= c->opt.refine_below || finf <= c->opt.tol)) {
+            if ((rc = residual_launch(c, u, c->d_F, outer, s))) return finish(rc);
+            count(outer);
+            norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
+            if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
+            f2 = c->h_pin[0];
+            finf = c->h_pin[1];
+            cur = outer;
+        }
         S.fnorm_2 = f2;
         S.fnorm_inf = finf;
         if (!isfinite(f2) || !isfinite(finf)) return finish(BFS_ENAN);
@@ -490,10 +507,9 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             return finish(BFS_ETIMEOUT);
         // the finite difference must subtract a residual of the same arithmetic
         const double *Fbase = c->d_F;
-        if (c->opt.krylov_precision != c->opt.outer_precision) {
+        if (c->opt.krylov_precision != cur) {
             if ((rc = residual_launch(c, u, c->d_F32, c->opt.krylov_precision, s))) return finish(rc);
-            if (c->opt.krylov_precision == BFS_FP32C) S.residual_evals_fp32++;
-            else S.residual_evals_fp64++;
+            count(c->opt.krylov_precision);
             Fbase = c->d_F32;
         }
         Gm gk{};
@@ -519,8 +535,8 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         while (mu >= 1e-4) {
             k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_ut, u, c->d_du, n, 1.0, mu, nullptr);
             c->launches++;
-            if ((rc = residual_launch(c, c->d_ut, c->d_Ft, c->opt.outer_precision, s))) return finish(rc);
-            S.residual_evals_fp64++;
+            if ((rc = residual_launch(c, c->d_ut, c->d_Ft, cur, s))) return finish(rc);
+            count(cur);
             norms_launch(c, c->d_Ft, n, c->d_scal + 12, c->d_scal + 13, s);
             if ((rc = read_scalars(c, c->d_scal + 12, 2, s))) return finish(rc);
             if (isfinite(c->h_pin[0]) && c->h_pin[0] <= (1.0 - 1e-4 * mu) * f2) {

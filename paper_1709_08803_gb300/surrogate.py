@@ -230,7 +230,7 @@ def bin_context(ctxs, mesh, topo, F, opts, bin_width=0.02):
 def solver_options(tol: float = 1e-8, budget_s: float = 3.0):
     return bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=1e-2, max_newton=25, max_krylov=200, time_budget_s=budget_s,
-                               precond_precision=bfs.BFS_FP32C)
+                               precond_precision=bfs.BFS_FP32C, refine_below=1e-5)
 
 
 def generate(n: int, seed: int, mesh=None, tol: float = 1e-8, log=None):
