@@ -210,8 +210,9 @@ def run_batch(args):
     __graft_entry__.build()
     meshes, topos, Fs = W.config_batch(seed=3, B=args.batch)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=args.eta, max_newton=30, max_krylov=150, time_budget_s=60.0,
-                               precond_precision=_pc_prec(args), refine_below=args.refine_below)
+                               eta=args.eta, max_newton=30, max_krylov=80, time_budget_s=60.0,
+                               precond_precision=_pc_prec(args), refine_below=args.refine_below,
+                               stall_newton=3)
     t0 = time.perf_counter()
     b = bfs.Batch(meshes, topos, Fs, opts)
     setup_s = time.perf_counter() - t0

@@ -105,6 +105,10 @@ typedef struct {
                               outer_precision for the final steps (iterative
                               refinement); convergence is only ever accepted on an
                               outer_precision residual.  0 (default): always outer. */
+    int stall_newton;      /* > 0: give up with BFS_ENOCONV once GMRES has ended above
+                              its forcing tolerance (max_krylov reached) in this many
+                              consecutive Newton steps -- the signature of a problem
+                              with no nearby steady solution.  0 (default): off. */
 } bfs_options;
 
 typedef struct {

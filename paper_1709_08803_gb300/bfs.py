@@ -51,7 +51,7 @@ class bfs_options(ctypes.Structure):
                 ("krylov_precision", ctypes.c_int), ("jv_h_rel", ctypes.c_double),
                 ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
                 ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int),
-                ("refine_below", ctypes.c_double)]
+                ("refine_below", ctypes.c_double), ("stall_newton", ctypes.c_int)]
 
 
 class bfs_stats(ctypes.Structure):

@@ -86,6 +86,7 @@ void bfs_default_options(bfs_options *o)
     o->outer_precision = BFS_FP64;
     o->precond_precision = BFS_FP64;
     o->refine_below = 0.0;
+    o->stall_newton = 0;
 }
 
 const char *bfs_last_error(const bfs_ctx *c) { return c ? c->err.c_str() : g_setup_err.c_str(); }

@@ -342,6 +342,7 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
     std::vector<bfs::Gm> g(B);
     std::vector<int> status(B, 1);  // 1 running, else final status
     std::vector<double> f2(B), finf(B), mu(B);
+    std::vector<int> stalls(B, 0);
     std::vector<int> all(B);
     std::iota(all.begin(), all.end(), 0);
 
@@ -471,7 +472,9 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
         std::vector<int> ls;
         for (int i : act) {
             S[i].krylov_its += g[i].its;
+            stalls[i] = g[i].res > g[i].target ? stalls[i] + 1 : 0;
             if (g[i].status != BFS_OK) status[i] = g[i].status;
+            else if (o.stall_newton > 0 && stalls[i] >= o.stall_newton) status[i] = BFS_ENOCONV;
             else { ls.push_back(i); mu[i] = 1.0; }
         }
         // lockstep backtracking line search

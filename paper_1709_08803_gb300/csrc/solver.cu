@@ -345,13 +345,13 @@ void gm_cycle_begin(bfs_ctx *c, Gm &g, double beta, cudaStream_t s)
 {
     const int m = c->m_alloc, n = c->n;
     if (!isfinite(beta)) { g.status = BFS_ENAN; g.state = Gm::DONE; return; }
+    g.res = beta;  // the true residual of the current iterate
     if (beta <= g.target || g.its >= g.maxit) { g.state = Gm::DONE; return; }
     k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V, c->d_w, n, c->d_scal + 8);
     c->launches++;
     k_gmres_init<<<1, 1, 0, s>>>(c->d_giv, m, c->d_scal + 8);
     c->launches++;
     g.j = 0;
-    g.res = beta;
     g.state = Gm::ARNOLDI;
 }
 
@@ -487,6 +487,7 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
     norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
     if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
     double f2 = c->h_pin[0], finf = c->h_pin[1];
+    int stalls = 0;
     for (int k = 0;; k++) {
         if (cur != outer && isfinite(finf) && (finf <= c->opt.refine_below || finf <= c->opt.tol)) {
             if ((rc = residual_launch(c, u, c->d_F, outer, s))) return finish(rc);
@@ -521,6 +522,11 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         g.precs = gk.precs;
         g.jvs = gk.jvs;
         if (rc) return finish(rc);
+        stalls = gk.res > gk.target ? stalls + 1 : 0;
+        if (c->opt.stall_newton > 0 && stalls >= c->opt.stall_newton) {
+            c->err = "GMRES stalled above its tolerance in consecutive Newton steps";
+            return finish(BFS_ENOCONV);
+        }
         {
             int fl = 0;
             BFS_CUDA_TRY(c, cudaMemcpyAsync(&fl, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));

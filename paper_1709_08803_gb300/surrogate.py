@@ -181,7 +181,8 @@ def scaled(topo, s: float):
     return W.Topography(-1.0 + s * (topo.beta + 1.0), s * topo.beta_x, s * topo.beta_y)
 
 
-def solve_with_continuation(ctx, topo, u0=None, stages=(1.0 / 3.0, 2.0 / 3.0, 1.0), direct_first=True):
+def solve_with_continuation(ctx, topo, u0=None, stages=(1.0 / 3.0, 2.0 / 3.0, 1.0), direct_first=True,
+                            on_stage=None):
     """Solve on ctx for `topo`: first directly from u0 (the uniform stream when
     None), and if that fails by continuation in bump height through `stages`,
     each stage starting from the previous solution (the paper's route to large
@@ -205,12 +206,15 @@ def solve_with_continuation(ctx, topo, u0=None, stages=(1.0 / 3.0, 2.0 / 3.0, 1.
     u = ctx.flat_guess()
     status = -1
     for sfac in stages:
-        ctx.set_topography(scaled(topo, sfac))
+        ts = scaled(topo, sfac)
+        ctx.set_topography(ts)
         st = ctx.solve(u, raise_on_error=False)
         add(st)
         status = st["status"]
         if status != 0:
             break
+        if on_stage is not None and sfac < 1.0:
+            on_stage(ts, u)
     return u, status, cost
 
 
@@ -228,42 +232,89 @@ def bin_context(ctxs, mesh, topo, F, opts, bin_width=0.02):
 
 
 def solver_options(tol: float = 1e-8, budget_s: float = 3.0):
+    """The mixed form with early exits: GMRES capped at 80 iterations per
+    Newton step and the solve abandoned after 3 consecutive Newton steps whose
+    GMRES ended above tolerance (most draws near F = 1 or with wide bumps have
+    no steady solution; this makes a failed attempt cost ~0.2 s, not seconds)."""
     return bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=1e-2, max_newton=25, max_krylov=200, time_budget_s=budget_s,
-                               precond_precision=bfs.BFS_FP32C, refine_below=1e-5)
+                               eta=1e-2, max_newton=25, max_krylov=80, time_budget_s=budget_s,
+                               precond_precision=bfs.BFS_FP32C, refine_below=1e-5, stall_newton=3)
 
 
-def generate(n: int, seed: int, mesh=None, tol: float = 1e-8, log=None):
-    """Solve n problems drawn from the batched-sweep distribution on `mesh`
-    (default 181 x 61), directly or by continuation in bump height.  Returns
-    (features [n, M, N, 4], targets [n, M, N, 3] = zeta, phi - x, psi - x,
-    records)."""
+def describe(topo_desc) -> dict:
+    kind, params = topo_desc
+    if kind == "ridge":
+        return {"kind": "ridge", "amp": params[0], "width": params[1]}
+    return {"kind": f"{len(params)} bumps", "amp": max(b[0] for b in params),
+            "width": max(b[1] for b in params)}
+
+
+def sample_problem_desc(rng, mesh):
+    """sample_problem plus a description of the draw (for the records)."""
+    F = float(rng.uniform(0.5, 1.4))
+    if rng.uniform() < 0.8:
+        nb = int(rng.integers(1, 4))
+        bumps = [(float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)),
+                  float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2))) for _ in range(nb)]
+        return W.gaussian_bumps(mesh, bumps), F, ("bumps", bumps)
+    rd = (float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)), float(rng.uniform(-2, 2)))
+    return W.gaussian_bumps(mesh, [], ridges=[rd]), F, ("ridge", rd)
+
+
+def generate(n: int, seed: int, mesh=None, tol: float = 1e-8, time_budget_s: float | None = None,
+             max_attempts: int | None = None, with_stages: bool = True, log=None):
+    """Draw problems from the batched-sweep distribution on `mesh` (default
+    181 x 61) and solve each directly, then by continuation in bump height,
+    until n solutions have been collected (or the time budget or attempt limit
+    runs out).  with_stages also keeps the converged intermediate stages of a
+    continuation (the same draw at 1/3 and 2/3 of its bump heights).
+    Returns (features [k, M, N, 4], targets [k, M, N, 3] = zeta, phi - x,
+    psi - x of the k solutions, records of every attempt)."""
     import torch
     mesh = mesh or W.config_paper_scale()[0]
     rng = np.random.default_rng(W.SEED_BASE + 7000 + seed)
-    probs = [sample_problem(rng, mesh) for _ in range(n)]
     xs = np.zeros((n, mesh.M, mesh.N, 4), dtype=np.float32)
     ys = np.zeros((n, mesh.M, mesh.N, 3), dtype=np.float32)
     recs, ctxs = [], {}
     opts = solver_options(tol)
     xg = torch.tensor(mesh.x(), device="cuda").view(1, -1)
     t0 = time.time()
-    for i, (topo, F) in enumerate(probs):
+    k = 0
+    stage_samples = 0
+
+    def keep(c, topo, F, u):
+        nonlocal k
+        if k >= n:
+            return
+        xs[k] = features(mesh, topo, F)
+        nv = c.unpack(u)
+        ys[k, :, :, 0] = nv["zeta"].float().cpu().numpy()
+        ys[k, :, :, 1] = (nv["phi"] - xg).float().cpu().numpy()
+        ys[k, :, :, 2] = (nv["psi"] - xg).float().cpu().numpy()
+        k += 1
+
+    while k < n:
+        if max_attempts is not None and len(recs) >= max_attempts:
+            break
+        if time_budget_s is not None and time.time() - t0 > time_budget_s:
+            break
+        topo, F, desc = sample_problem_desc(rng, mesh)
         c = bin_context(ctxs, mesh, topo, F, opts)
-        u, status, cost = solve_with_continuation(c, topo)
-        recs.append({"F": F, "status": status, **cost})
-        xs[i] = features(mesh, topo, F)
+        staged = []
+        u, status, cost = solve_with_continuation(
+            c, topo, on_stage=(lambda ts, us: staged.append((ts, us.clone()))) if with_stages else None)
+        recs.append({"F": F, "status": status, **describe(desc), **cost})
         if status == 0:
-            nv = c.unpack(u)
-            ys[i, :, :, 0] = nv["zeta"].float().cpu().numpy()
-            ys[i, :, :, 1] = (nv["phi"] - xg).float().cpu().numpy()
-            ys[i, :, :, 2] = (nv["psi"] - xg).float().cpu().numpy()
-        if log and (i + 1) % 50 == 0:
-            ok = sum(r["status"] == 0 for r in recs)
-            log(f"generated {i + 1}/{n} ({ok} converged) in {time.time() - t0:.1f} s")
+            keep(c, topo, F, u)
+        for ts, us in staged:  # converged intermediate amplitudes of this draw
+            keep(c, ts, F, us)
+            stage_samples += 1
+        if log and len(recs) % 100 == 0:
+            log(f"attempted {len(recs)}, collected {k} ({stage_samples} intermediate stages) "
+                f"in {time.time() - t0:.1f} s")
     for c in ctxs.values():
         c.close()
-    return xs, ys, recs
+    return xs[:k], ys[:k], recs
 
 
 def train(xs, ys, epochs: int = 60, batch: int = 16, lr: float = 2e-3, seed: int = 0, log=None):

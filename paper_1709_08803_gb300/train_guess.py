@@ -1,13 +1,15 @@
 """Train the learned initial guess on solutions the solver generates, and
 measure what it saves.
 
-    python -m paper_1709_08803_gb300.train_guess --train 2000 --test 200 \
-        --out paper_1709_08803_gb300/weights/cno_181x61.npz --report report.json
+    python -m paper_1709_08803_gb300.train_guess --train 2000 --gen-budget 1500 \
+        --test 200 --out paper_1709_08803_gb300/weights/cno_181x61.npz --report report.json
 
-1. draws train + test problems from the batched-sweep distribution (F ~ U[0.5,
-   1.4], 1-3 Gaussians or a ridge) on the 181 x 61 mesh and solves them with the
-   mixed JFNK solver (failures near the critical Froude number are counted and
-   left out of training);
+1. draws problems from the batched-sweep distribution (F ~ U[0.5, 1.4], 1-3
+   Gaussians or a ridge) on the 181 x 61 mesh and solves them with the mixed
+   JFNK solver, directly and then by continuation in bump height, until --train
+   of them have converged or --gen-budget seconds have passed (draws with no
+   steady solution the solver can reach -- most of those near F = 1, with wide
+   bumps or with ridges -- are counted and left out of training);
 2. trains the network (BF16 tensor-core kernels, Adam) on the converged ones;
 3. on the held-out problems, solves each from the uniform stream and from the
    network's guess and reports Newton iterations, Krylov iterations, residual
@@ -26,6 +28,7 @@ import numpy as np
 
 
 def evaluate(params, scale, n_test: int, seed: int, log=print):
+    """n_test held-out draws (attempts, converged or not) of the same distribution."""
     """Held-out problems, three arms: the network's guess (one direct solve;
     continuation from the uniform stream if it fails), continuation from the
     uniform stream (the baseline; a direct solve is tried first), and a single
@@ -38,14 +41,14 @@ def evaluate(params, scale, n_test: int, seed: int, log=print):
 
     mesh = W.config_paper_scale()[0]
     rng = np.random.default_rng(W.SEED_BASE + 9000 + seed)
-    probs = [S.sample_problem(rng, mesh) for _ in range(n_test)]
+    probs = [S.sample_problem_desc(rng, mesh) for _ in range(n_test)]
     net = S.CNO(mesh.M, mesh.N, 1)
     net.set_params(params, scale)
     opts = S.solver_options()
     ctxs, rows = {}, []
-    for i, (topo, F) in enumerate(probs):
+    for i, (topo, F, desc) in enumerate(probs):
         c = S.bin_context(ctxs, mesh, topo, F, opts)
-        rec = {"F": F}
+        rec = {"F": F, **S.describe(desc)}
         for arm in ("learned", "continuation", "flat"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -81,6 +84,7 @@ def evaluate(params, scale, n_test: int, seed: int, log=print):
     net.close()
     arms = ("learned", "continuation", "flat")
     both = [r for r in rows if r["learned"]["status"] == 0 and r["continuation"]["status"] == 0]
+    direct = [r for r in both if not r["learned"]["fallback"]]
 
     def mean(arm, k, rs):
         return float(np.mean([r[arm][k] for r in rs])) if rs else None
@@ -90,7 +94,11 @@ def evaluate(params, scale, n_test: int, seed: int, log=print):
         "failed": {a: sum(r[a]["status"] != 0 for r in rows) for a in arms},
         "learned_direct_success": sum(r["learned"]["status"] == 0 and not r["learned"]["fallback"] for r in rows),
         "learned_fallbacks": sum(r["learned"]["fallback"] for r in rows),
+        "converged": {a: sum(r[a]["status"] == 0 for r in rows) for a in arms},
         "mean_over_both_converged": {a: {k: mean(a, k, both) for k in ("newton", "krylov", "evals", "ms")}
+                                     for a in arms},
+        "learned_direct_and_continuation_converged": len(direct),
+        "mean_over_learned_direct": {a: {k: mean(a, k, direct) for k in ("newton", "krylov", "evals", "ms")}
                                      for a in arms},
     }
     if both:
@@ -103,7 +111,8 @@ def evaluate(params, scale, n_test: int, seed: int, log=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--train", type=int, default=2000, help="converged training solutions wanted")
+    ap.add_argument("--gen-budget", type=float, default=None, help="seconds allowed for data generation")
     ap.add_argument("--test", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--seed", type=int, default=0)
@@ -117,18 +126,21 @@ def main(argv=None):
 
     log = lambda m: print(m, file=sys.stderr, flush=True)
     t0 = time.time()
-    xs, ys, recs = S.generate(a.train, a.seed, log=log)
-    ok = np.array([r["status"] == 0 for r in recs])
+    xs, ys, recs = S.generate(a.train, a.seed, time_budget_s=a.gen_budget, log=log)
+    n_ok = xs.shape[0]
     gen_s = time.time() - t0
-    log(f"data: {ok.sum()} / {a.train} converged in {gen_s:.1f} s")
+    n_draws_ok = sum(r["status"] == 0 for r in recs)
+    log(f"data: {n_ok} solutions ({n_draws_ok} draws converged at full height) of {len(recs)} attempts "
+        f"in {gen_s:.1f} s")
     t0 = time.time()
-    params, scale, losses = S.train(xs[ok], ys[ok], epochs=a.epochs, seed=a.seed, log=log)
+    params, scale, losses = S.train(xs, ys, epochs=a.epochs, seed=a.seed, log=log)
     train_s = time.time() - t0
     out = a.out or S.WEIGHTS
-    S.save(out, params, scale, {"losses": losses, "train_size": int(ok.sum()), "epochs": a.epochs})
+    S.save(out, params, scale, {"losses": losses, "train_size": n_ok, "epochs": a.epochs})
     summary, rows = evaluate(params, scale, a.test, a.seed, log=log)
-    rep = {"train_requested": a.train, "train_converged": int(ok.sum()),
-           "train_failed_F": [r["F"] for r in recs if r["status"] != 0],
+    rep = {"train_requested": a.train, "train_solutions": n_ok, "train_attempts": len(recs),
+           "train_draws_converged": n_draws_ok,
+           "attempts": recs,
            "generate_s": gen_s, "train_s": train_s, "final_loss": losses[-1], "loss_curve": losses[::5],
            "weights": out, **summary}
     if a.report:
