@@ -41,6 +41,15 @@
  *       evaluated in a cancellation-free form where its log argument is small.
  *   R6  half domain: nodes with y >= 0, y1 = 0, mirrored images (x, -y) of the
  *       rows j >= 2 added as sources with zeta_y, beta_y negated.
+ *   R14 surface tension (Sec. 6 names the term, tension times mean curvature
+ *       in the dynamic condition, and leaves it to future work): F1 gains
+ *       -tau * kappa with kappa = div(grad zeta / sqrt(1 + |grad zeta|^2)),
+ *       expanded as ((1+zy^2) zxx - 2 zx zy zxy + (1+zx^2) zyy) / w^(3/2),
+ *       w = 1 + zx^2 + zy^2, at the half point: zx, zy its averages, zxx and
+ *       zxy the x-differences of the nodal zeta_x, zeta_y across it, zyy the
+ *       mean of the nodal second y-differences (central; second-order
+ *       one-sided on outer rows; mirror ghost on y = 0 of the half domain).
+ *       The linearised system gains -tau (zxx + zyy).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -61,6 +70,9 @@ typedef struct {
     const double *psurf;   /* applied surface pressure at the nodes, or NULL
                               (the pressure-distribution problem of Sec. 4.1:
                               p adds to the dynamic condition) */
+    double tau;            /* surface tension parameter (0: none): the dynamic
+                              condition gains -tau * kappa, kappa the mean-curvature
+                              operator of the surface (Sec. 6, reading R14) */
 } orc_problem;
 
 typedef struct {
@@ -126,6 +138,31 @@ static void orc_ydiff(const orc_problem *P, const double *q, double *qy)
 #undef Q
             qy[(size_t)j * N + i] = v;
         }
+}
+
+/* Second y-derivative of the nodal field q at node (i, j) (reading R14):
+   central (q_{j-1} - 2 q_j + q_{j+1}) / dy^2 inside; on an outer row the
+   second-order one-sided (2 q_0 - 5 q_1 + 4 q_2 - q_3) / dy^2 (first-order
+   q_0 - 2 q_1 + q_2 when M = 3); on y = 0 of the half domain the mirror ghost
+   q_{-1} = q_1 gives (2 q_1 - 2 q_0) / dy^2. */
+static double orc_yy(const orc_problem *P, const double *q, int i, int j)
+{
+    int N = P->N, M = P->M;
+    double h2 = P->dy * P->dy;
+#define Q(jj) q[(size_t)(jj) * N + i]
+    double v;
+    if (j == 0) {
+        if (P->half) v = 2.0 * (Q(1) - Q(0));
+        else if (M >= 4) v = 2.0 * Q(0) - 5.0 * Q(1) + 4.0 * Q(2) - Q(3);
+        else v = Q(0) - 2.0 * Q(1) + Q(2);
+    } else if (j == M - 1) {
+        if (M >= 4) v = 2.0 * Q(M - 1) - 5.0 * Q(M - 2) + 4.0 * Q(M - 3) - Q(M - 4);
+        else v = Q(M - 1) - 2.0 * Q(M - 2) + Q(M - 3);
+    } else {
+        v = Q(j - 1) - 2.0 * Q(j) + Q(j + 1);
+    }
+#undef Q
+    return v / h2;
 }
 
 /* ------------------------------------------------------------------ */
@@ -374,6 +411,19 @@ void orc_residual(const orc_problem *P, const double *beta, const double *bx, co
         double J = orc_bie_point(P, &top, &bot, 1, &Tb, &sc7);
         Fout[orc_row_F7(P, k, l)] = J - 2.0 * ORC_PI * gs;
         Fout[orc_row_F1(P, k, l)] = orc_bernoulli(P->F, zs, zxs, zys, pxs, pys, &sc1);
+        if (P->tau != 0.0) {
+            /* mean curvature at the half point: zeta_xx, zeta_xy as x-differences
+               of the nodal zeta_x, zeta_y across the half point, zeta_yy the mean
+               of the two nodal second y-differences (reading R14) */
+            double zxx = (nd.zx[b] - nd.zx[a]) / P->dx;
+            double zxy = (nd.zy[b] - nd.zy[a]) / P->dx;
+            double zyy = 0.5 * (orc_yy(P, nd.z, k, l) + orc_yy(P, nd.z, k + 1, l));
+            double w = 1.0 + zxs * zxs + zys * zys;
+            double kap = ((1.0 + zys * zys) * zxx - 2.0 * zxs * zys * zxy + (1.0 + zxs * zxs) * zyy) /
+                         (w * sqrt(w));
+            Fout[orc_row_F1(P, k, l)] -= P->tau * kap;
+            sc1 += fabs(P->tau * kap);
+        }
         if (P->psurf) {
             double pstar = 0.5 * (P->psurf[a] + P->psurf[b]);
             Fout[orc_row_F1(P, k, l)] += pstar;
@@ -449,6 +499,9 @@ void orc_residual_linear(const orc_problem *P, const double *bx, const double *u
             }
         double iK5 = orc_rect_S2(1.0, 0.0, 1.0, P->x1 - xs, xhi - xs, ylo - ys, yhi - ys);
         Fout[orc_row_F1(P, k, l)] = pxs + zs / (P->F * P->F) - 1.0;
+        if (P->tau != 0.0) /* linearised curvature: zeta_xx + zeta_yy */
+            Fout[orc_row_F1(P, k, l)] -= P->tau * ((nd.zx[b] - nd.zx[a]) / P->dx +
+                                                    0.5 * (orc_yy(P, nd.z, k, l) + orc_yy(P, nd.z, k + 1, l)));
         Fout[orc_row_F2(P, k, l)] = s2 + zxs * iK5 - 2.0 * ORC_PI * fs;
         Fout[orc_row_F7(P, k, l)] = s7 + P->sigma * bxs * iK5 - 2.0 * ORC_PI * gs;
     }

@@ -17,6 +17,9 @@ Parity status of each function (how it is pinned, see tests/test_oracle_pins.py)
   bottom_pressure .... hydrostatic value at the uniform stream; Bernoulli on a
                        streamsurface of a linear potential; force = 0 with
                        no bottom slope
+  surface tension .... the curvature term converges at second order to the
+                       mean curvature of an explicit surface (differentiated
+                       symbolically); linearisation identity with tau
 """
 from __future__ import annotations
 
@@ -49,7 +52,8 @@ class Problem(ctypes.Structure):
                 ("x1", ctypes.c_double), ("y1", ctypes.c_double),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("F", ctypes.c_double), ("n_rad", ctypes.c_double),
-                ("sigma", ctypes.c_double), ("psurf", ctypes.POINTER(ctypes.c_double))]
+                ("sigma", ctypes.c_double), ("psurf", ctypes.POINTER(ctypes.c_double)),
+                ("tau", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -114,11 +118,11 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def problem(mesh, F: float, sigma: float = -1.0, n_rad: float = 0.05, psurf=None) -> Problem:
+def problem(mesh, F: float, sigma: float = -1.0, n_rad: float = 0.05, psurf=None, tau: float = 0.0) -> Problem:
     """psurf: optional applied surface pressure at the nodes (kept alive on the
-    returned structure)."""
+    returned structure); tau: surface tension parameter (mean-curvature term)."""
     P = Problem(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy,
-                float(F), float(n_rad), float(sigma), None)
+                float(F), float(n_rad), float(sigma), None, float(tau))
     if psurf is not None:
         P._psurf = _f64(psurf).ravel().copy()
         P.psurf = _p(P._psurf)

@@ -210,10 +210,13 @@ def test_dynamic_condition_on_streamsurface():
 # flat bottom, the finite-difference Jacobian of the NONLINEAR residual equals
 # the Jacobian of the LINEAR discrete system of App. B.
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tau", [0.0, 0.4])
 @pytest.mark.parametrize("half", [0, 1])
-def test_linearisation_identity(half):
+def test_linearisation_identity(half, tau):
+    """tau > 0: the surface-tension term linearises to -tau (zeta_xx + zeta_yy)
+    in the linear system, consistently with the nonlinear curvature term."""
     mesh = W.mesh_box(13, 7, 0.4, 0.4, half=half)
-    P = O.problem(mesh, 0.7)
+    P = O.problem(mesh, 0.7, tau=tau)
     Jfd = O.fd_jacobian(P, W.flat_topography(mesh), W.flat_guess(mesh))
     Jt = O.jtilde(P)
     assert np.abs(Jfd - Jt).max() < 1e-6 * np.abs(Jt).max()
@@ -493,3 +496,48 @@ def test_pressure_patch_matches_bump_in_linear_regime():
         pred = zb - F * F * p
         errs.append(np.abs(zp - pred).max() / np.abs(pred).max())
     assert errs[0] < 1e-2 and errs[1] < errs[0]
+
+
+# ---------------------------------------------------------------------------
+# Surface tension (Sec. 6: tension times mean curvature in the dynamic
+# condition).  The oracle's curvature term, read off as F1(tau) - F1(0) at an
+# explicit surface, converges at second order to the mean curvature
+# div(grad zeta / sqrt(1 + |grad zeta|^2)) obtained by symbolic
+# differentiation of that definition (not of the expanded formula the oracle
+# uses), in the full and the half domain.
+# ---------------------------------------------------------------------------
+def _gaussian_surface_u(mesh, A, s, x0, y0):
+    sp = pytest.importorskip("sympy")
+    X, Y = sp.symbols("x y", real=True)
+    z = A * sp.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / s ** 2)
+    zx, zy = sp.diff(z, X), sp.diff(z, Y)
+    q = sp.sqrt(1 + zx ** 2 + zy ** 2)
+    kappa = sp.diff(zx / q, X) + sp.diff(zy / q, Y)
+    f_z, f_zx, f_k = (sp.lambdify((X, Y), e, "numpy") for e in (z, zx, kappa))
+    x, y = mesh.x(), mesh.y()
+    NB = mesh.N + 1
+    u = W.flat_guess(mesh).copy()
+    for j in range(mesh.M):  # zeta block: zeta(1) then zeta_x at every node
+        u[j * NB] = f_z(x[0], y[j])
+        u[j * NB + 1: j * NB + 1 + mesh.N] = f_zx(x, np.full_like(x, y[j]))
+    xs = x[:-1] + 0.5 * mesh.dx
+    kap = np.array([[f_k(xx, yy) for xx in xs] for yy in y])  # [M, N-1]
+    return u, kap
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_surface_tension_term_is_the_mean_curvature(half):
+    errs = []
+    for h in (0.2, 0.1):
+        L, H = 4.0, 3.0
+        N, M = int(round(2 * L / h)) + 1, (int(round(H / h)) + 1 if half else int(round(2 * H / h)) + 1)
+        mesh = W.Mesh(N=N, M=M, x1=-L, y1=0.0 if half else -H, dx=h, dy=h, half=half)
+        u, kap = _gaussian_surface_u(mesh, 0.5, 1.3, 0.3, 0.0 if half else 0.4)  # slopes to 0.33
+        topo = W.flat_topography(mesh)
+        r0 = O.residual(O.problem(mesh, 0.8), topo, u)
+        r1 = O.residual(O.problem(mesh, 0.8, tau=1.0), topo, u)
+        NB = N + 1
+        got = np.array([[-(r1[l * NB + 2 + k] - r0[l * NB + 2 + k]) for k in range(N - 1)] for l in range(M)])
+        errs.append(np.abs(got - kap).max() / np.abs(kap).max())
+    assert errs[1] < 1e-2, errs
+    assert errs[0] / errs[1] > 3.0, errs  # second order
