@@ -69,8 +69,11 @@ typedef struct {
 } bfs_mesh;
 
 /* Bottom z = beta(x, y) and its exact derivatives at the N*M nodes, index
-   i + N*j (0-based), HOST arrays, copied by bfs_setup.  beta must stay below
-   the undisturbed surface (beta < 0) and tend to -1 far away (Sec. 2.1). */
+   i + N*j (0-based), HOST arrays, copied by bfs_setup.  beta tends to -1 far
+   away (Sec. 2.1) and must stay below F^2/2: Bernoulli bounds every surface
+   height by F^2/2 (the speed cannot be imaginary), so a bottom reaching it
+   pierces the surface.  A bottom above z = 0 is allowed (the supercritical
+   solutions of Sec. 5.2 flow over bumps taller than the upstream depth). */
 typedef struct {
     const double *beta, *beta_x, *beta_y;
 } bfs_topo;
@@ -98,7 +101,10 @@ typedef struct {
                               of the preconditioner sweeps.  The factorisation is FP64
                               either way; FP32C sweeps an FP32 copy of the factors
                               (the preconditioner only steers GMRES, the Newton
-                              residual and the converged u do not depend on it) */
+                              residual and the converged u do not depend on it).
+                              With surface_tension > 0 the sweeps stay FP64: the
+                              capillary term leaves the factors too ill-conditioned
+                              for FP32 copies. */
     double refine_below;   /* > 0 with outer_precision != krylov_precision: the Newton
                               residual and the line search use the Krylov arithmetic
                               while |F|_inf > refine_below, then switch to
@@ -109,6 +115,11 @@ typedef struct {
                               its forcing tolerance (max_krylov reached) in this many
                               consecutive Newton steps -- the signature of a problem
                               with no nearby steady solution.  0 (default): off. */
+    double surface_tension; /* tau >= 0: the dynamic condition gains -tau * kappa,
+                              kappa the mean curvature operator div(grad zeta /
+                              sqrt(1 + |grad zeta|^2)) at the half points (the
+                              extension Sec. 6 proposes); the preconditioner gains the
+                              linearised term -tau (zeta_xx + zeta_yy).  0 (default). */
 } bfs_options;
 
 typedef struct {
@@ -133,7 +144,7 @@ void bfs_default_options(bfs_options *o);
    that depend only on the bottom (the single-layer sum over the bottom seen
    from bottom collocation points, Sec. 3.1).  Synchronous.  Errors:
    BFS_EINVAL for N < 4, M < 3, dx or dy <= 0, F <= 0, half_domain with
-   y1 != 0, beta >= 0 anywhere or a non-finite input; BFS_ENOMEM; BFS_ECUDA. */
+   y1 != 0, beta >= F^2/2 anywhere or a non-finite input; BFS_ENOMEM; BFS_ECUDA. */
 int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_options *opt,
               bfs_ctx **out);
 

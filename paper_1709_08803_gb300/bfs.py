@@ -51,7 +51,8 @@ class bfs_options(ctypes.Structure):
                 ("krylov_precision", ctypes.c_int), ("jv_h_rel", ctypes.c_double),
                 ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
                 ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int),
-                ("refine_below", ctypes.c_double), ("stall_newton", ctypes.c_int)]
+                ("refine_below", ctypes.c_double), ("stall_newton", ctypes.c_int),
+                ("surface_tension", ctypes.c_double)]
 
 
 class bfs_stats(ctypes.Structure):

@@ -87,6 +87,7 @@ void bfs_default_options(bfs_options *o)
     o->precond_precision = BFS_FP64;
     o->refine_below = 0.0;
     o->stall_newton = 0;
+    o->surface_tension = 0.0;
 }
 
 const char *bfs_last_error(const bfs_ctx *c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -122,6 +123,8 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     if (o.krylov_precision != BFS_FP64 && o.krylov_precision != BFS_FP32C && o.krylov_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "unknown krylov_precision");
     if (!(o.refine_below >= 0.0)) return set_err(nullptr, BFS_EINVAL, "refine_below must be >= 0");
+    if (!(o.surface_tension >= 0.0) || !isfinite(o.surface_tension))
+        return set_err(nullptr, BFS_EINVAL, "surface_tension must be finite and >= 0");
     if (o.precond_precision != BFS_FP64 && o.precond_precision != BFS_FP32C)
         return set_err(nullptr, BFS_EINVAL, "precond_precision must be BFS_FP64 or BFS_FP32C");
     if (o.outer_precision != BFS_FP64 && o.outer_precision != BFS_DF64)
@@ -130,8 +133,8 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     for (size_t q = 0; q < NM; q++) {
         if (!isfinite(topo->beta[q]) || !isfinite(topo->beta_x[q]) || !isfinite(topo->beta_y[q]))
             return set_err(nullptr, BFS_EINVAL, "topography has a non-finite value");
-        if (!(topo->beta[q] < 0.0))
-            return set_err(nullptr, BFS_EINVAL, "the bottom must stay below z = 0 (beta < 0)");
+        if (!(topo->beta[q] < 0.5 * F * F))
+            return set_err(nullptr, BFS_EINVAL, "the bottom reaches F^2/2, above any possible free surface");
     }
 
     bfs_ctx *c = new (std::nothrow) bfs_ctx();
@@ -202,10 +205,11 @@ int bfs_set_topography(bfs_ctx *c, const bfs_topo *topo)
     for (size_t q = 0; q < NM; q++) {
         if (!isfinite(topo->beta[q]) || !isfinite(topo->beta_x[q]) || !isfinite(topo->beta_y[q]))
             return set_err(c, BFS_EINVAL, "topography has a non-finite value");
-        if (!(topo->beta[q] < 0.0))
-            return set_err(c, BFS_EINVAL, "the bottom must stay below z = 0 (beta < 0)");
+        if (!(topo->beta[q] < 0.5 * c->F * c->F))
+            return set_err(c, BFS_EINVAL, "the bottom reaches F^2/2, above any possible free surface");
     }
     BFS_CUDA_TRY(c, cudaDeviceSynchronize());
+    bfs::gm_graphs_clear(c);
     BFS_CUDA_TRY(c, cudaMemcpy(c->d_beta, topo->beta, sizeof(double) * NM, cudaMemcpyHostToDevice));
     BFS_CUDA_TRY(c, cudaMemcpy(c->d_bx, topo->beta_x, sizeof(double) * NM, cudaMemcpyHostToDevice));
     BFS_CUDA_TRY(c, cudaMemcpy(c->d_by, topo->beta_y, sizeof(double) * NM, cudaMemcpyHostToDevice));
@@ -220,6 +224,8 @@ int bfs_set_topography(bfs_ctx *c, const bfs_topo *topo)
 int bfs_set_surface_pressure(bfs_ctx *c, const double *p)
 {
     if (!c) return BFS_EINVAL;
+    cudaDeviceSynchronize();
+    bfs::gm_graphs_clear(c);
     if (!p) {
         cudaFree(c->d_psurf);
         c->d_psurf = nullptr;
@@ -240,6 +246,7 @@ int bfs_set_froude(bfs_ctx *c, double F)
 {
     if (!c) return BFS_EINVAL;
     if (!(F > 0.0) || !isfinite(F)) return set_err(c, BFS_EINVAL, "F must be positive");
+    bfs::gm_graphs_clear(c);  // F is an argument of the captured finish kernels
     c->F = F;
     return BFS_OK;
 }
@@ -247,6 +254,8 @@ int bfs_set_froude(bfs_ctx *c, double F)
 void bfs_destroy(bfs_ctx *c)
 {
     if (!c) return;
+    cudaDeviceSynchronize();
+    bfs::gm_graphs_clear(c);
     free_all(c);
     delete c;
 }

@@ -45,7 +45,8 @@ struct FlowArgs {
     int nb, NB, M, h;
     int ldp;                       // padded row length of the FP32 factors (multiple of 4)
     int nslot;                     // shared-memory ring depth (TMA kernel)
-    unsigned int tag0;             // tag of step s is tag0 + s
+    unsigned int *tagp;            // device word: tag of this launch's step 0; step s writes
+                                   // tag0 + s, and block 0 advances the word by 2M on exit
     int *flag;
 };
 
@@ -66,6 +67,22 @@ __device__ __forceinline__ void st_word(unsigned long long *p, float v, unsigned
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
+__device__ __forceinline__ unsigned int ld_tag(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Block 0 ends after every CTA has stored its rows of step 2M-2, so every
+// CTA has read the launch's tag by then: the next launch may use the next
+// 2M tags.
+__device__ __forceinline__ void advance_tag(unsigned int *p, unsigned int tag0, int M)
+{
+    const unsigned int next = tag0 + 2u * (unsigned int)M;
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(next) : "memory");
+}
+
 // Value of a tagged entry once its tag is `tag`; false on timeout.
 __device__ __forceinline__ bool await_word(const unsigned long long *p, unsigned int tag, float &v)
 {
@@ -84,9 +101,14 @@ template <int RPC, int CPT>
 __global__ void __launch_bounds__(FL_TPB, 1) k_apply_flow(FlowArgs a)
 {
     __shared__ float red[RPC][FL_WARPS];
+    __shared__ unsigned int tag_sh;
     const float *pc = a.pc;
     const int nb = a.nb, NB = a.NB, M = a.M, h = a.h, nd = 2 * h + 1, G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if ((int)blockIdx.x >= nb) return;  // no rows here
+    if (tid == 0) tag_sh = ld_tag(a.tagp);
+    __syncthreads();
+    const unsigned int tag0 = tag_sh;
 
     int row[RPC];
     bool rv[RPC];
@@ -174,7 +196,7 @@ __global__ void __launch_bounds__(FL_TPB, 1) k_apply_flow(FlowArgs a)
                 const int mm = (bb == 0 || !two) ? m : m2;
                 const bool use = bb == 0 || two;
                 const unsigned long long *vp = vec(pass, k, mm);
-                const unsigned int tg = a.tag0 + producer(pass, k, mm);
+                const unsigned int tg = tag0 + producer(pass, k, mm);
 #pragma unroll
                 for (int q = 0; q < CPT; q++) {
                     v[bb][q] = 0.f;
@@ -213,7 +235,7 @@ __global__ void __launch_bounds__(FL_TPB, 1) k_apply_flow(FlowArgs a)
             }
             const float sg = (pass == 1 && crit == k) ? 1.f : -1.f;
             const unsigned long long *vp = vec(pass, k, crit);
-            const unsigned int tg = a.tag0 + (unsigned int)(s - 1);
+            const unsigned int tg = tag0 + (unsigned int)(s - 1);
             float v[CPT];
 #pragma unroll
             for (int q = 0; q < CPT; q++) {
@@ -236,7 +258,10 @@ __global__ void __launch_bounds__(FL_TPB, 1) k_apply_flow(FlowArgs a)
             if (lane == 0) red[j][warp] = t;
         }
         if (!__syncthreads_and(ok)) {
-            if (tid == 0) atomicOr(a.flag, 2);
+            if (tid == 0) {
+                atomicOr(a.flag, 2);
+                if (blockIdx.x == 0) advance_tag(a.tagp, tag0, M);
+            }
             return;
         }
         if (my_rv) {
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(FL_TPB, 1) k_apply_flow(FlowArgs a)
 #pragma unroll
             for (int w = 0; w < FL_WARPS; w++) t += red[my_j][w];
             const size_t si = (size_t)k * nb + blockIdx.x + my_j * G;
-            const unsigned int tg = a.tag0 + (unsigned int)s;
+            const unsigned int tg = tag0 + (unsigned int)s;
             if (pass == 0) {
                 st_word(a.Y + si, (float)(xk + (double)t), tg);
             } else {
@@ -254,6 +279,7 @@ __global__ void __launch_bounds__(FL_TPB, 1) k_apply_flow(FlowArgs a)
         }
         __syncthreads();  // red is rewritten by the next step
     }
+    if (blockIdx.x == 0 && tid == 0) advance_tag(a.tagp, tag0, M);
 }
 
 // TMA variant for slice blocks that fit its tiles (rows per CTA <= RPC,
@@ -316,6 +342,7 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
     extern __shared__ __align__(128) float ring[];  // nslot x BMAX x RPC x ldp
     __shared__ __align__(8) unsigned long long full[MAXSLOT], empty[MAXSLOT];
     __shared__ float red[2][RPC][WARPS];
+    __shared__ unsigned int tag_sh;
     const float *pc = a.pc;
     const int nb = a.nb, NB = a.NB, M = a.M, h = a.h, nd = 2 * h + 1, ldp = a.ldp;
     const int nslot = a.nslot, G = gridDim.x;
@@ -335,7 +362,9 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
         return (p <= h && m <= M - 1) ? m : -1;
     };
 
+    if (nrv == 0) return;  // no rows here
     if (tid == 0) {
+        tag_sh = ld_tag(a.tagp);
         for (int i = 0; i < nslot; i++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])) : "memory");
@@ -343,6 +372,7 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const unsigned int tag0 = tag_sh;
 
     if (warp == WARPS) {
         // producer warp: lane L copies row L % RPC of position L / RPC
@@ -449,8 +479,8 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
             for (int q = 0; q < CPT; q++) {
                 v[q] = 0.f;
                 if (cv[q]) {
-                    if ((unsigned int)(yw[q] >> 32) == a.tag0 + (unsigned int)k) v[q] = __uint_as_float((unsigned int)yw[q]);
-                    else if (ok) ok = await_word(a.Y + (size_t)k * nb + col[q], a.tag0 + (unsigned int)k, v[q]);
+                    if ((unsigned int)(yw[q] >> 32) == tag0 + (unsigned int)k) v[q] = __uint_as_float((unsigned int)yw[q]);
+                    else if (ok) ok = await_word(a.Y + (size_t)k * nb + col[q], tag0 + (unsigned int)k, v[q]);
                 }
             }
             dot(S, 0, v, acc, 1.f);
@@ -460,7 +490,7 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
         if (ok && (turn || pos_m(s, 1) >= 0)) {
             const unsigned long long *vp = turn ? a.Y + (size_t)k * nb
                                                 : (pass == 0 ? a.Y + (size_t)(k - 1) * nb : a.X + (size_t)(k + 1) * nb);
-            const unsigned int tg = a.tag0 + (unsigned int)(s - 1);
+            const unsigned int tg = tag0 + (unsigned int)(s - 1);
             float v[CPT];
 #pragma unroll
             for (int q = 0; q < CPT; q++) {
@@ -494,7 +524,10 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
             if (lane == 0) rd[j][warp] = u;
         }
         if (!compute_sync_and(ok, CT)) {
-            if (tid == 0) atomicOr(a.flag, 2);
+            if (tid == 0) {
+                atomicOr(a.flag, 2);
+                if (blockIdx.x == 0) advance_tag(a.tagp, tag0, M);
+            }
             return;  // the producer drains its copies and returns
         }
         if (tid == 0)  // every compute warp has read slot `slot`
@@ -504,7 +537,7 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
 #pragma unroll
             for (int w = 0; w < WARPS; w++) u += rd[my_j][w];
             const size_t si = (size_t)k * nb + r0 + my_j;
-            const unsigned int tg = a.tag0 + (unsigned int)s;
+            const unsigned int tg = tag0 + (unsigned int)s;
             if (pass == 0) {
                 st_word(a.Y + si, (float)(xk + (double)u), tg);
             } else {
@@ -521,6 +554,7 @@ __global__ void __launch_bounds__(CT + 32, 1) k_apply_tma(FlowArgs a)
         // red[s & 1] is next written at step s + 2, after every thread has
         // passed the barrier of step s + 1
     }
+    if (blockIdx.x == 0 && tid == 0) advance_tag(a.tagp, tag0, M);
 }
 
 constexpr int TMA_CT = 288, TMA_RPC = 4, TMA_CPT = 2, TMA_BMAX = 4, TMA_MAXSLOT = 8;
@@ -549,6 +583,30 @@ __global__ void k_cast_f32(const double *__restrict__ in, float *__restrict__ ou
     }
 }
 
+__global__ void k_set_tag(unsigned int *p, unsigned int v) { *p = v; }
+
+// Zero the tagged vectors and restart the tags at 1 (so no stale entry can
+// carry a tag a later launch waits for).
+static int flow_reset(bfs_ctx *c, cudaStream_t s)
+{
+    const size_t nv = (size_t)c->M * c->nb;
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flow, 0, sizeof(unsigned long long) * (2 * nv + 1), s));
+    k_set_tag<<<1, 1, 0, s>>>(reinterpret_cast<unsigned int *>(c->d_flow + 2 * nv), 1u);
+    c->launches++;
+    c->flow_count = 0;
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// Before each FP32 sweep launch (direct or inside a graph): restart the tags
+// well before they could wrap.
+int flow_wrap_check(bfs_ctx *c, cudaStream_t s)
+{
+    const unsigned long long steps = 2ull * (unsigned long long)c->M;
+    if ((c->flow_count + 2) * steps >= 0xFFFFFFFFull - 0xFFFFull) return flow_reset(c, s);
+    return BFS_OK;
+}
+
 int precond_make_f32(bfs_ctx *c, cudaStream_t s)
 {
     const int ldp = (c->nb + 3) / 4 * 4;
@@ -561,13 +619,13 @@ int precond_make_f32(bfs_ctx *c, cudaStream_t s)
     c->d_pc32 = nullptr;
     c->d_flow = nullptr;
     if (cudaMalloc(&c->d_pc32, sizeof(float) * cnt) != cudaSuccess ||
-        cudaMalloc(&c->d_flow, sizeof(unsigned long long) * 2 * nv) != cudaSuccess) {
+        cudaMalloc(&c->d_flow, sizeof(unsigned long long) * (2 * nv + 1)) != cudaSuccess) {
         cudaGetLastError();
         c->err = "FP32 preconditioner copy: out of device memory";
         return BFS_ENOMEM;
     }
-    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flow, 0, sizeof(unsigned long long) * 2 * nv, s));
-    c->flow_tag = 1;
+    int rc = flow_reset(c, s);
+    if (rc) return rc;
     k_cast_f32<<<4 * num_sms(c->device), 256, 0, s>>>(c->d_pc, c->d_pc32, rows, c->nb, ldp);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());
@@ -598,10 +656,9 @@ int apply_flow_launch(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
         if (per_sm < 1) return 0;
         c->flow_checked = 1;
     }
-    const unsigned int steps = 2u * (unsigned int)c->M;
-    if (c->flow_tag > 0xFFFFFFFFu - steps - 1u) {  // tags would wrap: start over from zeroed buffers
-        BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flow, 0, sizeof(unsigned long long) * 2 * (size_t)c->M * c->nb, s));
-        c->flow_tag = 1;
+    if (!c->capturing) {
+        int rc = flow_wrap_check(c, s);
+        if (rc) return rc;
     }
     FlowArgs a;
     a.pc = c->d_pc32;
@@ -611,12 +668,12 @@ int apply_flow_launch(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
     a.nb = c->nb; a.NB = c->N + 1; a.M = c->M; a.h = c->pc_h;
     a.ldp = c->ldp32;
     a.nslot = nslot;
-    a.tag0 = c->flow_tag;
+    a.tagp = reinterpret_cast<unsigned int *>(c->d_flow + 2 * (size_t)c->M * c->nb);
     a.flag = c->d_flag;
     void *args[] = {&a};
     BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(tpb), args, dyn, s));
     c->launches++;
-    c->flow_tag += steps;
+    c->flow_count++;
     return 1;
 }
 

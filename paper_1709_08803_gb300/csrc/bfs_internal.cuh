@@ -103,8 +103,17 @@ struct bfs_ctx {
     int pc_ready, pc_h, nb, apply_grid;
     double *d_pc;      // M * (2h+1) * nb * nb  block-banded factors
     float *d_pc32;     // FP32 copy of d_pc (precond_precision FP32C)
-    unsigned long long *d_flow;  // tagged y and z of the FP32 sweeps, 2 M nb
-    unsigned int flow_tag;       // tag of the next sweep launch's first step
+    unsigned long long *d_flow;  // tagged y and z of the FP32 sweeps, 2 M nb, then the tag word
+    unsigned long long flow_count;  // FP32 sweep launches since the tags were reset
+    int capturing;               // a CUDA graph is being captured on the solver stream
+
+    // Arnoldi steps of bfs_solve replayed as CUDA graphs, one per (Krylov
+    // index j, base residual buffer); cleared whenever a captured argument
+    // could change (factor, F, topography, surface pressure, u buffer)
+    std::vector<cudaGraphExec_t> gm_exec;
+    std::vector<unsigned long long> gm_nlaunch, gm_nflow;
+    const double *gm_u;
+    int gm_warm, gm_disabled;
     int ldp32;                   // padded row length of d_pc32
     int flow_checked;
     double *d_gj;      // 2 * nb * 2nb  Gauss-Jordan ping-pong
@@ -136,6 +145,7 @@ int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s);
 // apply.cu
 int precond_make_f32(bfs_ctx *c, cudaStream_t s);
 int apply_flow_launch(bfs_ctx *c, const double *r, double *z, cudaStream_t s);
+int flow_wrap_check(bfs_ctx *c, cudaStream_t s);
 extern const BatchVariant kBatchVariants[];
 extern const int kNumBatchVariants;
 int batch_pairs_occupancy(int v, int *blocks_per_sm);
@@ -171,6 +181,7 @@ void solver_axpby(bfs_ctx *c, double *y, const double *x, const double *z, doubl
 int jvp_launch(bfs_ctx *c, const double *u, const double *Fu, const double *z, double *Jz,
                double h, int precision, cudaStream_t s, bool unorm_ready = false);
 int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s);
+void gm_graphs_clear(bfs_ctx *c);
 int alloc_solver(bfs_ctx *c);
 void norms_launch(bfs_ctx *c, const double *v, int n, double *d_out2, double *d_outinf, cudaStream_t s);
 

@@ -46,7 +46,7 @@ __device__ double rect_S2_pc(double s1, double s2, double t1, double t2);
 
 struct PcArgs {
     int N, M, half, h, nb;
-    double x1, y1, dx, dy, F, n_rad, xhi, ylo, yhi;
+    double x1, y1, dx, dy, F, n_rad, xhi, ylo, yhi, tau;
 };
 
 __device__ __forceinline__ double trap_w(const PcArgs &a, int i, int j)  // 0-based
@@ -175,6 +175,46 @@ __global__ void k_form_sparse(PcArgs a, double *pc)
     } else {  // F2 (phi) or F7 (psi): -2 pi (q* - x*)
         row[f * NB + 0] = -TWO_PI;
         for (int p = 1; p <= a.N; p++) row[f * NB + p] = -TWO_PI * dx * half_H(k, p);
+    }
+}
+
+// Surface tension in the F1 rows: -tau (zeta_xx* + zeta_yy*) with zeta_xx* the
+// x-difference of zeta_x across the half point and zeta_yy* the mean of the
+// nodal second y-differences; the nodal zeta of slice l' is zeta(1) + dx times
+// the trapezoid weights of zeta_x, so each stencil row l' adds entries to
+// block (l, l') when it lies in the band.  One thread per F1 row.
+__global__ void k_form_tension(PcArgs a, double *pc)
+{
+    const int N = a.N, M = a.M, NB = a.N + 1, nb = a.nb, h = a.h;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * (N - 1)) return;
+    const int l = e / (N - 1), k = e % (N - 1) + 1;  // k 1-based
+    const size_t r = (size_t)(k + 1) * nb;             // row of F1(k) in its slice block
+    auto block = [&](int lp) { return pc + ((size_t)l * (2 * h + 1) + (lp - l + h)) * nb * nb; };
+    double *d = block(l);
+    d[r + k] += a.tau / a.dx;
+    d[r + k + 1] -= a.tau / a.dx;
+    int js[4];
+    double cs[4];
+    int ns = 0;
+    if (l == 0) {
+        if (a.half) { js[0] = 0; cs[0] = -2.0; js[1] = 1; cs[1] = 2.0; ns = 2; }
+        else if (M >= 4) { js[0] = 0; cs[0] = 2.0; js[1] = 1; cs[1] = -5.0; js[2] = 2; cs[2] = 4.0; js[3] = 3; cs[3] = -1.0; ns = 4; }
+        else { js[0] = 0; cs[0] = 1.0; js[1] = 1; cs[1] = -2.0; js[2] = 2; cs[2] = 1.0; ns = 3; }
+    } else if (l == M - 1) {
+        if (M >= 4) { js[0] = M - 1; cs[0] = 2.0; js[1] = M - 2; cs[1] = -5.0; js[2] = M - 3; cs[2] = 4.0; js[3] = M - 4; cs[3] = -1.0; ns = 4; }
+        else { js[0] = M - 1; cs[0] = 1.0; js[1] = M - 2; cs[1] = -2.0; js[2] = M - 3; cs[2] = 1.0; ns = 3; }
+    } else {
+        js[0] = l - 1; cs[0] = 1.0; js[1] = l; cs[1] = -2.0; js[2] = l + 1; cs[2] = 1.0; ns = 3;
+    }
+    const double f = -a.tau / (a.dy * a.dy);
+    for (int q = 0; q < ns; q++) {
+        const int lp = js[q];
+        if (lp - l > h || l - lp > h) continue;  // outside the band (App. A)
+        double *row = block(lp) + r;
+        const double c = f * cs[q];
+        row[0] += c;
+        for (int p = 1; p <= N; p++) row[p] += c * a.dx * half_H(k, p);
     }
 }
 
@@ -541,11 +581,13 @@ static PcArgs pc_args(const bfs_ctx *c, int h)
     a.xhi = c->x1 + (c->N - 1) * c->dx;
     a.yhi = c->y1 + (c->M - 1) * c->dy;
     a.ylo = c->half ? -a.yhi : c->y1;
+    a.tau = c->opt.surface_tension;
     return a;
 }
 
 void precond_free(bfs_ctx *c)
 {
+    gm_graphs_clear(c);  // the graphs captured the factor and sweep buffers
     cudaFree(c->d_pc);
     cudaFree(c->d_pc32);
     cudaFree(c->d_flow);
@@ -592,6 +634,10 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     c->launches++;
     k_form_sparse<<<(M * nb + 127) / 128, 128, 0, s>>>(a, c->d_pc);
     c->launches++;
+    if (a.tau != 0.0) {
+        k_form_tension<<<(M * (c->N - 1) + 127) / 128, 128, 0, s>>>(a, c->d_pc);
+        c->launches++;
+    }
     BFS_CUDA_TRY(c, cudaGetLastError());
 
     auto B = [&](int l, int m) { return c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz; };
@@ -653,7 +699,10 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
         c->err = "zero pivot in a diagonal block of the preconditioner";
         return BFS_ESINGULAR;
     }
-    if (c->opt.precond_precision == BFS_FP32C) {
+    // FP32 sweeps only without surface tension: the capillary term makes the
+    // diagonal blocks so ill-conditioned (inverse entries of 1e5-1e7 on small
+    // meshes) that FP32 copies of the factors no longer precondition
+    if (c->opt.precond_precision == BFS_FP32C && c->opt.surface_tension == 0.0) {
         int rc = precond_make_f32(c, s);
         if (rc) return rc;
         BFS_CUDA_TRY(c, cudaStreamSynchronize(s));

@@ -332,9 +332,32 @@ __device__ double rect_S2(double A, double B, double C, double s1, double s2, do
 }
 
 struct FinArgs {
-    int N, M, Nt, splits;
-    double x1, y1, dx, dy, ylo, yhi, xhi, F, n_rad;
+    int N, M, Nt, splits, half;
+    double x1, y1, dx, dy, ylo, yhi, xhi, F, n_rad, tau;
 };
+
+// Second y-difference of nodal zeta at node (i, j): central inside,
+// second-order one-sided on an outer row (first order when M = 3), mirror
+// ghost on y = 0 of the half domain.
+__device__ __forceinline__ double zeta_yy(const double *__restrict__ z, int N, int M, int half, double dy, int i,
+                                          int j)
+{
+    const double *c = z + i;
+    double v;
+    if (j == 0) {
+        if (half) v = 2.0 * (c[(size_t)N] - c[0]);
+        else if (M >= 4) v = 2.0 * c[0] - 5.0 * c[(size_t)N] + 4.0 * c[2 * (size_t)N] - c[3 * (size_t)N];
+        else v = c[0] - 2.0 * c[(size_t)N] + c[2 * (size_t)N];
+    } else if (j == M - 1) {
+        const double *e = c + (size_t)(M - 1) * N;
+        if (M >= 4) v = 2.0 * e[0] - 5.0 * e[-(long)N] + 4.0 * e[-2 * (long)N] - e[-3 * (long)N];
+        else v = e[0] - 2.0 * e[-(long)N] + e[-2 * (long)N];
+    } else {
+        const double *e = c + (size_t)j * N;
+        v = e[-(long)N] - 2.0 * e[0] + e[(size_t)N];
+    }
+    return v / (dy * dy);
+}
 
 // F2 / F7 / F1 at every half point (four lanes per target: the split partial
 // sums and the four corners of the closed-form integral are spread over the
@@ -383,6 +406,15 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
         const double num = (1.0 + zxs * zxs) * pys * pys + (1.0 + zys * zys) * pxs * pxs -
                            2.0 * zxs * zys * pxs * pys;
         double F1 = 0.5 * num / (1.0 + zxs * zxs + zys * zys) + zs / (a.F * a.F) - 0.5;
+        if (a.tau != 0.0) {  // surface tension: -tau times the mean curvature at the half point
+            const size_t NM = (size_t)N * M, qa = (size_t)l * N + k;
+            const double zxx = (nodal[NM + qa + 1] - nodal[NM + qa]) / a.dx;
+            const double zxy = (nodal[2 * NM + qa + 1] - nodal[2 * NM + qa]) / a.dx;
+            const double zyy = 0.5 * (zeta_yy(nodal, N, M, a.half, a.dy, k, l) +
+                                      zeta_yy(nodal, N, M, a.half, a.dy, k + 1, l));
+            const double w = 1.0 + zxs * zxs + zys * zys;
+            F1 -= a.tau * ((1.0 + zys * zys) * zxx - 2.0 * zxs * zys * zxy + (1.0 + zxs * zxs) * zyy) / (w * sqrt(w));
+        }
         if (psurf) {  // applied surface pressure at the half point (Sec. 4.1)
             const size_t qa = (size_t)l * N + k;
             F1 += 0.5 * (psurf[qa] + psurf[qa + 1]);
@@ -461,7 +493,8 @@ static RecArgs rec_args(const bfs_ctx *c)
 static FinArgs fin_args(const bfs_ctx *c, int splits)
 {
     FinArgs a;
-    a.N = c->N; a.M = c->M; a.Nt = c->Nt; a.splits = splits;
+    a.N = c->N; a.M = c->M; a.Nt = c->Nt; a.splits = splits; a.half = c->half;
+    a.tau = c->opt.surface_tension;
     a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy;
     a.yhi = c->y1 + (c->M - 1) * c->dy;
     a.ylo = c->half ? -a.yhi : c->y1;

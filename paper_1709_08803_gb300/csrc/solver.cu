@@ -426,6 +426,68 @@ int gm_restart_post(bfs_ctx *c, Gm &g, cudaStream_t s)
     return BFS_OK;
 }
 
+void gm_graphs_clear(bfs_ctx *c)
+{
+    for (cudaGraphExec_t e : c->gm_exec)
+        if (e) cudaGraphExecDestroy(e);
+    c->gm_exec.clear();
+    c->gm_nlaunch.clear();
+    c->gm_nflow.clear();
+    c->gm_u = nullptr;
+}
+
+// The Arnoldi step of Krylov index g.j as a graph (captured on first use):
+// P^-1 v_j, u + h z, F(u + h z), J z, CGS2, v_{j+1}, Givens -- about twenty
+// kernels launched as one.  Returns null when graphs are off (profiling, or a
+// capture that failed), and the caller launches the kernels one by one.
+static cudaGraphExec_t arnoldi_graph(bfs_ctx *c, Gm &g, cudaStream_t s, size_t &key)
+{
+    if (c->prof_on || c->gm_disabled || !c->gm_warm) return nullptr;
+    if (g.u != c->gm_u) {
+        gm_graphs_clear(c);
+        c->gm_u = g.u;
+    }
+    key = 2 * (size_t)g.j + (g.Fbase == c->d_F ? 0 : 1);
+    if (key >= c->gm_exec.size()) {
+        c->gm_exec.resize(key + 1, nullptr);
+        c->gm_nlaunch.resize(key + 1, 0);
+        c->gm_nflow.resize(key + 1, 0);
+    }
+    if (c->gm_exec[key]) return c->gm_exec[key];
+    const unsigned long long l0 = c->launches, f0 = c->flow_count;
+    const int p0 = g.precs, j0 = g.jvs;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->gm_disabled = 1;
+        return nullptr;
+    }
+    c->capturing = 1;
+    int rc = gm_arnoldi_pre(c, g, s);
+    if (!rc) rc = residual_launch(c, c->d_up, c->d_Fp, c->opt.krylov_precision, s);
+    if (!rc) rc = gm_arnoldi_post(c, g, s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    c->capturing = 0;
+    const unsigned long long nl = c->launches - l0, nf = c->flow_count - f0;
+    c->launches = l0;
+    c->flow_count = f0;
+    g.precs = p0;
+    g.jvs = j0;
+    cudaGraphExec_t ex = nullptr;
+    if (!rc && e == cudaSuccess && graph && cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess) {
+        c->gm_exec[key] = ex;
+        c->gm_nlaunch[key] = nl;
+        c->gm_nflow[key] = nf;
+    } else {
+        ex = nullptr;
+        c->gm_disabled = 1;  // launch one by one from now on
+        c->err.clear();
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return ex;
+}
+
 // One instance: the phases above with the residual evaluated in between.
 static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s)
 {
@@ -435,9 +497,21 @@ static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s)
     gm_cycle_begin(c, g, c->h_pin[0], s);
     while (g.state != Gm::DONE) {
         if (g.state == Gm::ARNOLDI) {
-            if ((rc = gm_arnoldi_pre(c, g, s))) return rc;
-            if ((rc = residual_launch(c, c->d_up, c->d_Fp, kp, s))) return rc;
-            if ((rc = gm_arnoldi_post(c, g, s))) return rc;
+            size_t key = 0;
+            cudaGraphExec_t ex = arnoldi_graph(c, g, s, key);
+            if (ex) {
+                if ((rc = flow_wrap_check(c, s))) return rc;
+                BFS_CUDA_TRY(c, cudaGraphLaunch(ex, s));
+                c->launches += c->gm_nlaunch[key];
+                c->flow_count += c->gm_nflow[key];
+                g.precs++;
+                g.jvs++;
+            } else {
+                if ((rc = gm_arnoldi_pre(c, g, s))) return rc;
+                if ((rc = residual_launch(c, c->d_up, c->d_Fp, kp, s))) return rc;
+                if ((rc = gm_arnoldi_post(c, g, s))) return rc;
+                c->gm_warm = 1;
+            }
             if ((rc = read_scalars(c, c->d_scal + 8, 2, s))) return rc;
             gm_arnoldi_host(c, g, c->h_pin[0], c->h_pin[1]);
         } else if (g.state == Gm::CYCLE_END) {
@@ -555,7 +629,8 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         f2 = c->h_pin[0];
         finf = c->h_pin[1];
         BFS_CUDA_TRY(c, cudaMemcpyAsync(u, c->d_ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        std::swap(c->d_F, c->d_Ft);
+        // copy rather than swap: d_F stays the buffer the Arnoldi graphs captured
+        BFS_CUDA_TRY(c, cudaMemcpyAsync(c->d_F, c->d_Ft, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         S.newton_its = k + 1;
     }
 }

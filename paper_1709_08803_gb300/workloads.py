@@ -159,6 +159,24 @@ def config_large():
     return mesh, topo, 0.9
 
 
+def config_supercritical_281(eps: float = 0.1):
+    """The paper's supercritical runs (Sec. 5.2, Fig. 5): 281 x 281 nodes,
+    x in [-21, 51], y in [-36, 36] (dx = dy = 72/280 = 0.257), F = 3, one
+    Gaussian bump of width delta = 3 at the origin with height eps."""
+    h = 72.0 / 280.0
+    mesh = Mesh(N=281, M=281, x1=-21.0, y1=-36.0, dx=h, dy=h, half=0)
+    return mesh, gaussian_bumps(mesh, [(eps, 3.0, 0.0, 0.0)]), 3.0
+
+
+def config_subcritical_281(eps: float = 0.1):
+    """The paper's subcritical runs (Sec. 5.1, Fig. 4): 281 x 281 nodes,
+    x in [-7, 17], y in [-12, 12] (dx = dy = 24/280 = 0.0857), F = 0.6, one
+    Gaussian bump of width delta = 0.5 at the origin with height eps."""
+    h = 24.0 / 280.0
+    mesh = Mesh(N=281, M=281, x1=-7.0, y1=-12.0, dx=h, dy=h, half=0)
+    return mesh, gaussian_bumps(mesh, [(eps, 0.5, 0.0, 0.0)]), 0.6
+
+
 def mesh_box(N: int, M: int, dx: float, dy: float, half: int = 0, x1: float | None = None) -> Mesh:
     """A mesh of N x M nodes with the upstream edge at about 28% of the
     x-extent upstream of the origin, symmetric in y."""

@@ -74,7 +74,7 @@ def test_setup_rejects_invalid_input(L, case):
     elif case == "half_y1":
         mesh = W.Mesh(N=9, M=5, x1=-1, y1=-0.4, dx=0.4, dy=0.4, half=1)
     elif case == "beta_pierces":
-        topo = W.gaussian_bumps(mesh, [(1.2, 0.7, 0.0, 0.0)])
+        topo = W.gaussian_bumps(mesh, [(1.0 + 0.5 * F * F + 0.05, 0.7, 0.0, 0.0)])  # top above F^2/2
     elif case == "nan":
         b = topo.beta.copy()
         b[3] = np.nan
