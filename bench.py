@@ -195,6 +195,53 @@ def run_residual(args):
     return 0
 
 
+def run_apply(args):
+    """Preconditioner sweeps only (z = P^-1 r) at 181 x 61 in the mixed form's
+    arithmetic (FP32 sweeps over the FP32 copy of the factors): the dominant
+    kernel of the solve, timed alone with CUDA events (burst HBM peak)."""
+    import torch
+
+    import __graft_entry__
+    from paper_1709_08803_gb300 import bfs
+    from paper_1709_08803_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    __graft_entry__.build()
+    mesh, topo, F = W.config_paper_scale(args.F)
+    ctx = bfs.Context(mesh, topo, F, bfs.default_options(precond_precision=_pc_prec(args)))
+    ctx.precond_factor()
+    r = torch.tensor(W.perturbed_guess(mesh, 3, 1.0), dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    for _ in range(args.warmup):
+        ctx.precond_apply(r, out=z)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record()
+    for _ in range(args.steps):
+        ctx.precond_apply(r, out=z)
+    ev1.record()
+    torch.cuda.nvtx.range_pop()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    h = max(1, round(mesh.M / 20))
+    nb = 3 * (mesh.N + 1)
+    blocks = sum(min(k, h) + 1 + min(mesh.M - 1 - k, h) for k in range(mesh.M))
+    esz = 4 if args.precond == "fp32" else 8
+    nbytes = blocks * nb * nb * esz + 6 * ctx.n * 8
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ach = nbytes / (ms / 1e3) / 1e9
+    print(json.dumps({"mode": "apply", "metric": "preconditioner sweeps at 181x61", "unit": "ms",
+                      "value": ms, "steps": args.steps, "warmup": args.warmup,
+                      "sweep_steps": 2 * mesh.M, "us_per_sweep_step": ms * 1e3 / (2 * mesh.M),
+                      "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                   "frac": ach / hbm, "algorithmic_bytes": nbytes,
+                                   "peak_source": f"hbm_gbs of the {src} peaks file"}}))
+    ctx.close()
+    return 0
+
+
 def run_batch(args):
     """Batched sweep: args.batch instances (F ~ U[0.5, 1.4], 1-3 Gaussians or a
     ridge, meshes 61x21 ... 241x81) solved in lockstep; one step = one batched
@@ -289,7 +336,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true",
                     help="time the solve from the uniform stream even when trained weights exist")
-    ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch", "apply"],
                     help="solve: the JFNK step; residual: residual evaluations only; "
                          "batch: the 64-instance batched sweep")
     ap.add_argument("--batch", type=int, default=64, help="instances in --mode batch")
@@ -298,6 +345,8 @@ def main():
         return run_reference(args)
     if args.mode == "residual":
         return run_residual(args)
+    if args.mode == "apply":
+        return run_apply(args)
     if args.mode == "batch":
         return run_batch(args)
 
@@ -376,6 +425,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     step_ms, evals, stats = [], 0, []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.fill_(1.0)  # L2 flush between steps (not timed)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -387,6 +437,7 @@ def main():
         step_ms.append(ev0.elapsed_time(ev1))
         stats.append(st)
         evals += st["residual_evals_fp64"] + st["residual_evals_fp32"]
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     _, launches1 = ctx.profile_read()
     clocks = sampler.stop()
@@ -492,7 +543,9 @@ def main():
     achieved = INSTR_PER_INDEX_PAIR * n_index_pairs / (avg32 / 1e3) / 1e12 if n32 else None
     roofline_pairs = {"bound": "alu", "kernel": "k_pairs<float> (FP32C all-pairs quadrature)",
                 "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                "frac": (achieved / peak_tinst) if achieved else None, "traffic": None,
+                "frac": (achieved / peak_tinst) if achieved else None,
+                # dram bytes read + written per launch, ncu (profiles/k_pairs_181x61.md)
+                "traffic": 1.43e6 if args.F == 0.7 else None,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz (max SM clock, {src} peaks file)",
                 "avg_launch_ms": avg32, "launches": n32,
                 "fp64_pair_kernel_avg_ms": ms64 / max(n64, 1) if n64 else None,
@@ -513,7 +566,9 @@ def main():
                       "us_per_sweep_step": avg_ap * 1e3 / (2 * mesh.M) if nap else None,
                       "achieved": apply_bytes / (avg_ap / 1e3) / 1e9 if nap else None, "peak": hbm,
                       "unit": "GB/s", "frac": (apply_bytes / (avg_ap / 1e3) / 1e9) / hbm if nap else None,
-                      "traffic": None, "algorithmic_bytes": apply_bytes, "avg_launch_ms": avg_ap,
+                      # dram bytes read + written per launch, ncu (profiles/k_apply_tma_181x61.md)
+                      "traffic": 501.1e6 if (esz == 4 and args.F == 0.7) else None,
+                      "algorithmic_bytes": apply_bytes, "avg_launch_ms": avg_ap,
                       "launches": nap, "peak_source": f"hbm_gbs of the {src} peaks file",
                       "share_of_step": msap / (prof_wall_ms * prof_steps)}
     roofline = roofline_apply if msap > ms32 + msdf + ms64 else roofline_pairs
