@@ -108,7 +108,7 @@ int batched_residual32(bfs_batch *b, const std::vector<const double *> &u, const
 {
     int rc;
     for (int i = 0; i < b->B; i++)
-        if ((rc = bfs::unpack_launch(b->c[i], u[i], s))) return berr(b, rc, b->c[i]->err);
+        if ((rc = bfs::unpack_launch(b->c[i], u[i], s, 2))) return berr(b, rc, b->c[i]->err);
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), s) != cudaSuccess)
         return berr(b, BFS_ECUDA, "queue reset failed");
     bfs::batch_pairs_launch(v, grid, b->d_inst, b->d_items[v], b->n_items[v], b->d_counter, b->d_mask, s);

@@ -135,7 +135,7 @@ namespace bfs {
 
 // residual.cu
 int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cudaStream_t s);
-int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s);
+int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s, int which = 3);
 int constB_launch(bfs_ctx *c, cudaStream_t s);
 PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, int sms);
 void plans_for(int Nt, int Ns, int splits_req, int sms, PairPlan *p64, PairPlan *p32);

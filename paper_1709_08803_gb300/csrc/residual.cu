@@ -66,6 +66,7 @@ __device__ __forceinline__ double ydiff(const double *q, int N, int M, int half,
 
 struct RecArgs {
     int N, M, half, Ns, Ns_cap, Nt;
+    int w64, w32;  // which source-record copies to write (a residual reads one)
     double x1, y1, dx, dy, sigma, jc, ry;
 };
 
@@ -120,10 +121,10 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
             for (int k = 0; k < REC; k++) r[k] = 0.0;
             r[0] = 1.0e6;
         }
-        for (int k = 0; k < REC; k++) {
-            src64[(size_t)e * REC + k] = r[k];
-            src32[(size_t)e * REC + k] = (float)r[k];
-        }
+        if (a.w64)
+            for (int k = 0; k < REC; k++) src64[(size_t)e * REC + k] = r[k];
+        if (a.w32)
+            for (int k = 0; k < REC; k++) src32[(size_t)e * REC + k] = (float)r[k];
         return;
     }
     e -= a.Ns_cap;
@@ -359,9 +360,12 @@ __device__ __forceinline__ double zeta_yy(const double *__restrict__ z, int N, i
     return v / (dy * dy);
 }
 
-// F2 / F7 / F1 at every half point (four lanes per target: the split partial
-// sums and the four corners of the closed-form integral are spread over the
-// lanes), radiation rows per slice.
+constexpr int FIN_LANES = 4;  // lanes per target in k_finish: the four corners of the closed form
+                               // (FP64 logs; more lanes leave FP64 warp slots idle)
+
+// F2 / F7 / F1 at every half point (FIN_LANES lanes per target share the
+// split partial sums; lanes 0-3 also take the four corners of the closed-form
+// integral), radiation rows per slice.
 __global__ void k_finish(const double *__restrict__ part, const double *__restrict__ tgt,
                          const double *__restrict__ constB, const double *__restrict__ nodal,
                          const double *__restrict__ psurf, double *__restrict__ Fu,
@@ -369,7 +373,7 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
 {
     const double TWO_PI = 6.283185307179586476925286766559;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int e = g >> 2, q4 = g & 3;
+    const int e = g / FIN_LANES, q4 = g % FIN_LANES;
     const int N = a.N, M = a.M;
     const size_t blk = (size_t)(N + 1) * M;
     bool bad = false;
@@ -379,8 +383,8 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
 #pragma unroll
     for (int q = 0; q < NACC; q++) acc[q] = 0.0;
     if (is_t) {
-#pragma unroll 4
-        for (int s = q4; s < a.splits; s += 4)
+#pragma unroll 2
+        for (int s = q4; s < a.splits; s += FIN_LANES)
 #pragma unroll
             for (int q = 0; q < NACC; q++) acc[q] += part[((size_t)s * NACC + q) * a.Nt + et];
     }
@@ -391,9 +395,9 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
     // corner q4 of the rectangle: (s2,t2) +, (s1,t2) -, (s2,t1) -, (s1,t1) +
     const double sc = (q4 & 1) ? a.x1 - xs : a.xhi - xs;
     const double tc = (q4 & 2) ? a.ylo - ys : a.yhi - ys;
-    double g2 = (is_t ? antideriv_S2(A, B, C, sc, tc) : 0.0) * (((q4 == 1) || (q4 == 2)) ? -1.0 : 1.0);
+    double g2 = (is_t && q4 < 4 ? antideriv_S2(A, B, C, sc, tc) : 0.0) * (((q4 == 1) || (q4 == 2)) ? -1.0 : 1.0);
 #pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
+    for (int o = 1; o < FIN_LANES; o <<= 1) {
         g2 += __shfl_xor_sync(0xffffffffu, g2, o);
 #pragma unroll
         for (int q = 0; q < NACC; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
@@ -487,6 +491,7 @@ static RecArgs rec_args(const bfs_ctx *c)
     a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy; a.sigma = c->opt.sign_I4;
     a.jc = c->half ? 0.0 : 0.5 * (c->M - 1);
     a.ry = c->dy / c->dx;
+    a.w64 = a.w32 = 1;
     return a;
 }
 
@@ -518,11 +523,13 @@ PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, 
     return p;
 }
 
-int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s)
+int unpack_launch(bfs_ctx *c, const double *u, cudaStream_t s, int which)
 {
     k_unpack<<<(3 * c->M * 32 + 127) / 128, 128, 0, s>>>(u, c->d_nodal, c->N, c->M, c->dx);
     c->launches++;
     RecArgs ra = rec_args(c);
+    ra.w64 = which & 1;
+    ra.w32 = (which >> 1) & 1;
     int tot = c->Ns_cap + c->Nt;
     k_records<<<(tot + 255) / 256, 256, 0, s>>>(c->d_nodal, c->d_beta, c->d_bx, c->d_by, c->d_src64,
                                                  c->d_src32, c->d_tgt64, c->d_tgt32, ra);
@@ -537,7 +544,8 @@ constexpr int P32_TPB = 128, P32_TPT = 2, P32_CH = 128;
 
 int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cudaStream_t s)
 {
-    int rc = unpack_launch(c, u, s);
+    // FP32C pairs read the FP32 source records, FP64 and double-float ones the FP64 records
+    int rc = unpack_launch(c, u, s, precision == BFS_FP32C ? 2 : 1);
     if (rc) return rc;
     const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
     dim3 grid(p.tiles, p.splits);
@@ -559,7 +567,7 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
     if (precision != BFS_DF64) c->launches++;
     if (ev1) cudaEventRecord(ev1, s);
     FinArgs fa = fin_args(c, p.splits);
-    int tot = 4 * (c->Nt + c->M);
+    int tot = FIN_LANES * (c->Nt + c->M);
     k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
                                                c->d_flag, fa);
     c->launches++;
@@ -571,7 +579,7 @@ int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s)
 {
     const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
     FinArgs fa = fin_args(c, p.splits);
-    int tot = 4 * (c->Nt + c->M);
+    int tot = FIN_LANES * (c->Nt + c->M);
     k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
                                                c->d_flag, fa);
     c->launches++;
