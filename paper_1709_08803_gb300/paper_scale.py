@@ -2,7 +2,7 @@
 bump height, the paper's route to its large-amplitude solutions.
 
     python -m paper_1709_08803_gb300.paper_scale --case super \
-        --eps 0.1 0.5 1.0 1.5 2.0 2.5 2.75 --out super.json
+        --eps 0.1 0.5 1.0 1.25 1.5 1.75 2.0 2.25 2.5 2.75 --max-newton 60 --out super.json
 
 Each stage starts from the previous stage's solution; the preconditioner is
 factored once (it does not depend on the bottom, Sec. 4.2).  Reported per
@@ -21,7 +21,7 @@ import time
 import numpy as np
 
 
-def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, log=print):
+def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: int = 40, log=print):
     import torch
 
     from . import bfs
@@ -30,7 +30,7 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, log=print):
     cfg = W.config_supercritical_281 if case == "super" else W.config_subcritical_281
     mesh, topo, F = cfg(eps_list[0])
     opts = bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=1e-2, max_newton=40, max_krylov=400, refine_below=1e-5,
+                               eta=1e-2, max_newton=max_newton, max_krylov=400, refine_below=1e-5,
                                precond_precision=bfs.BFS_FP32C, half_band=half_band)
     ctx = bfs.Context(mesh, topo, F, opts)
     t0 = time.perf_counter()
@@ -70,11 +70,13 @@ def main(argv=None):
     ap.add_argument("--case", default="super", choices=["super", "sub"])
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1, 0.5, 1.0, 1.5, 2.0, 2.5, 2.75])
     ap.add_argument("--half-band", type=int, default=3)
+    ap.add_argument("--max-newton", type=int, default=40)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     import __graft_entry__
     __graft_entry__.build()
-    rep = run(a.case, a.eps, a.half_band, log=lambda m: print(m, file=sys.stderr, flush=True))
+    rep = run(a.case, a.eps, a.half_band, max_newton=a.max_newton,
+              log=lambda m: print(m, file=sys.stderr, flush=True))
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(rep, fh, indent=1)
