@@ -39,6 +39,7 @@ void free_all(bfs_ctx *c)
     cudaFree(c->d_up);
     cudaFree(c->d_scal);
     cudaFree(c->d_red);
+    cudaFree(c->d_tailbar);
     cudaFree(c->d_V);
     cudaFree(c->d_H);
     cudaFree(c->d_giv);

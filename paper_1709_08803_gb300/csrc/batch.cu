@@ -377,7 +377,10 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
         return BFS_OK;
     };
 
-    for (int i = 0; i < B; i++) cudaMemsetAsync(b->c[i]->d_flag, 0, sizeof(int), s);
+    for (int i = 0; i < B; i++) {
+        cudaMemsetAsync(b->c[i]->d_flag, 0, sizeof(int), s);
+        cudaMemsetAsync(b->c[i]->d_tailbar, 0, 2 * sizeof(unsigned int), s);
+    }
     if ((rc = outer_residuals(all, false))) return rc;
     for (int i = 0; i < B; i++) { f2[i] = b->h_sc[4 * i]; finf[i] = b->h_sc[4 * i + 1]; }
 

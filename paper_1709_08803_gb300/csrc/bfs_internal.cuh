@@ -95,6 +95,8 @@ struct bfs_ctx {
     double *d_H;      // Hessenberg, column j at d_H + j (m+1)
     double *d_giv;    // cs[m], sn[m], g[m+1], y[m], h[m+1], h2[m+1]
     double *d_red;    // reduction partials
+    unsigned int *d_tailbar;  // grid barrier of the fused Arnoldi tail
+    int tail_grid;            // its grid (0: the kernels one by one)
     double *d_sbase;  // one allocation holding the n-vectors below
     double *d_F, *d_du, *d_ut, *d_Ft, *d_z, *d_w, *d_F32, *d_uio;  // n each
     double *h_pin;    // pinned host scalars

@@ -235,13 +235,13 @@ __global__ void k_scale_into(double *__restrict__ out, const double *__restrict_
 // Givens step for column j: H(0..j, j) = h + h2, H(j+1, j) = |w|; rotate with
 // the stored rotations, form the new one, update g; residual estimate |g_{j+1}|
 // goes to res.  Layout of giv: cs[m] sn[m] g[m+1] y[m] h[m+1] h2[m+1].
-__global__ void k_givens(double *H, double *giv, int m, int j, const double *hn, double *res)
+__device__ void givens_step(double *H, double *giv, int m, int j, double hn, double *res)
 {
     double *cs = giv, *sn = giv + m, *g = giv + 2 * m, *h = giv + 4 * m + 1,
            *h2 = giv + 5 * m + 2;
     double *col = H + (size_t)j * (m + 1);
     for (int i = 0; i <= j; i++) col[i] = h[i] + h2[i];
-    col[j + 1] = *hn;
+    col[j + 1] = hn;
     for (int i = 0; i < j; i++) {
         double a = col[i], b = col[i + 1];
         col[i] = cs[i] * a + sn[i] * b;
@@ -256,6 +256,132 @@ __global__ void k_givens(double *H, double *giv, int m, int j, const double *hn,
     g[j + 1] = -sn[j] * g[j];
     g[j] = cs[j] * g[j];
     *res = fabs(g[j + 1]);
+}
+
+__global__ void k_givens(double *H, double *giv, int m, int j, const double *hn, double *res)
+{
+    givens_step(H, giv, m, j, *hn, res);
+}
+
+// ---------------------------------------------------------------------------
+// The tail of an Arnoldi step in one cooperative launch: two classical
+// Gram-Schmidt passes of w against V[0..cnt) (h, then h2), |w|, v_cnt = w/|w|
+// and the Givens step of column cnt-1.  CTA b owns the slice [b chunk,
+// (b+1) chunk) of the vectors; each dot product is reduced in a fixed order
+// (warp shuffles inside a CTA, then one CTA per dot over the CTA partials),
+// so the result does not depend on timing; values other CTAs wrote in this
+// launch are read past L1.  Six grid barriers, each a
+// bounded spin (about a second) that raises bit 2 of the flag on timeout.
+// ---------------------------------------------------------------------------
+struct TailBar {
+    unsigned int count, gen;
+};
+
+__device__ bool tail_sync(TailBar *b, int *flag)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = &b->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&b->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned int spins = 0;
+            while (*vgen == g) {
+                if (++spins > (1u << 24)) {
+                    atomicOr(flag, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok;
+}
+
+constexpr int TAIL_TPB = 256;
+
+struct TailArgs {
+    const double *V;
+    double *w, *Vnext, *H, *giv, *part, *hn, *res;
+    int n, cnt, m;
+    TailBar *bar;
+    int *flag;
+};
+
+__global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
+{
+    __shared__ double hs[128];
+    __shared__ double red[TAIL_TPB / 32];
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = a.n, cnt = a.cnt, m = a.m;
+    const int chunk = (n + G - 1) / G, e0 = b * chunk, e1 = min(n, e0 + chunk);
+    double *h = a.giv + 4 * m + 1, *h2 = a.giv + 5 * m + 2;
+    auto block_sum = [&](double v) {  // every thread gets the CTA total
+        v = warp_sum(v);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        double t = tid < TAIL_TPB / 32 ? red[tid] : 0.0;
+        if (warp == 0) t = warp_sum(t);
+        if (tid == 0) red[0] = t;
+        __syncthreads();
+        return red[0];
+    };
+    for (int pass = 0; pass < 2; pass++) {
+        double *hp = pass ? h2 : h;
+        // partial dots of this CTA's slice, one warp per dot
+        for (int i = warp; i < cnt; i += TAIL_TPB / 32) {
+            const double *vi = a.V + (size_t)i * n;
+            double acc = 0.0;
+            for (int e = e0 + lane; e < e1; e += 32) acc = fma(vi[e], a.w[e], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) a.part[(size_t)i * G + b] = acc;
+        }
+        if (!tail_sync(a.bar, a.flag)) return;
+        // dot i reduced by CTA i (fixed order over the CTA partials)
+        for (int i = b; i < cnt; i += G) {
+            double v = 0.0;
+            for (int q = tid; q < G; q += TAIL_TPB) v += __ldcg(a.part + (size_t)i * G + q);
+            v = block_sum(v);
+            if (tid == 0) hp[i] = v;
+        }
+        if (!tail_sync(a.bar, a.flag)) return;
+        for (int i = tid; i < cnt; i += TAIL_TPB) hs[i] = __ldcg(hp + i);
+        __syncthreads();
+        for (int e = e0 + tid; e < e1; e += TAIL_TPB) {
+            double acc = a.w[e];
+            for (int i = 0; i < cnt; i++) acc = fma(-hs[i], a.V[(size_t)i * n + e], acc);
+            a.w[e] = acc;
+        }
+        __syncthreads();  // the next pass reads w with a different thread mapping
+    }
+    // |w|
+    double s2 = 0.0;
+    for (int e = e0 + tid; e < e1; e += TAIL_TPB) s2 = fma(a.w[e], a.w[e], s2);
+    s2 = block_sum(s2);
+    if (tid == 0) a.part[b] = s2;
+    if (!tail_sync(a.bar, a.flag)) return;
+    if (b == 0) {
+        double v = 0.0;
+        for (int q = tid; q < G; q += TAIL_TPB) v += __ldcg(a.part + q);
+        v = block_sum(v);
+        if (tid == 0) *a.hn = sqrt(v);
+    }
+    if (!tail_sync(a.bar, a.flag)) return;
+    const double hn = __ldcg(a.hn);
+    const double sc = hn > 0.0 ? 1.0 / hn : 0.0;
+    for (int e = e0 + tid; e < e1; e += TAIL_TPB) a.Vnext[e] = a.w[e] * sc;
+    if (b == 0 && tid == 0) givens_step(a.H, a.giv, m, cnt - 1, hn, a.res);
 }
 
 // g = (beta, 0, ..., 0) and V_0 scale factor
@@ -291,6 +417,19 @@ int alloc_solver(bfs_ctx *c)
     c->d_z = b + 4 * (size_t)n; c->d_w = b + 5 * (size_t)n; c->d_F32 = b + 6 * (size_t)n;
     c->d_uio = b + 7 * (size_t)n;
     BFS_CUDA_TRY(c, cudaMallocHost(&c->h_pin, sizeof(double) * 16));
+    // the fused Arnoldi tail: one CTA per SM (its partials, one per CTA and
+    // dot, fit the reduction scratch of 32768 doubles for up to 128 dots)
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_tailbar, 2 * sizeof(unsigned int)));
+    BFS_CUDA_TRY(c, cudaMemset(c->d_tailbar, 0, 2 * sizeof(unsigned int)));
+    {
+        int per_sm = 0;
+        const int G = num_sms(c->device);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_tail, TAIL_TPB, 0) == cudaSuccess &&
+            per_sm >= 1 && (size_t)G * 129 <= 128 * 256)
+            c->tail_grid = G;
+        else
+            cudaGetLastError();
+    }
     return BFS_OK;
 }
 
@@ -371,6 +510,19 @@ int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s)
     int rc = jv_post(c, g.Fbase, c->d_w, s);
     if (rc) return rc;
     g.jvs++;
+    if (c->tail_grid > 0 && g.j + 1 <= 128) {
+        TailArgs ta;
+        ta.V = c->d_V; ta.w = c->d_w; ta.Vnext = c->d_V + (size_t)(g.j + 1) * n;
+        ta.H = c->d_H; ta.giv = c->d_giv; ta.part = c->d_red; ta.hn = c->d_scal + 8; ta.res = c->d_scal + 9;
+        ta.n = n; ta.cnt = g.j + 1; ta.m = m;
+        ta.bar = reinterpret_cast<TailBar *>(c->d_tailbar);
+        ta.flag = c->d_flag;
+        void *args[] = {&ta};
+        BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_arnoldi_tail, dim3(c->tail_grid),
+                                                    dim3(TAIL_TPB), args, 0, s));
+        c->launches++;
+        return BFS_OK;
+    }
     arnoldi_orth(c, g.j + 1, s);
     k_scale_into<<<grid_for(n), 256, 0, s>>>(c->d_V + (size_t)(g.j + 1) * n, c->d_w, n, c->d_scal + 8);
     c->launches++;
@@ -548,6 +700,8 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         return status;
     };
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+    // a barrier left half-way by a timed-out launch must not carry over
+    BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_tailbar, 0, 2 * sizeof(unsigned int), s));
     // arithmetic of the Newton residual and line search: the Krylov one while
     // |F| is large (refine_below > 0), the outer one for the final steps
     const int outer = c->opt.outer_precision;
