@@ -259,7 +259,7 @@ def run_batch(args):
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=args.eta, max_newton=30, max_krylov=80, time_budget_s=60.0,
                                precond_precision=_pc_prec(args), refine_below=args.refine_below,
-                               stall_newton=3)
+                               stall_newton=3, forcing=args.forcing)
     t0 = time.perf_counter()
     b = bfs.Batch(meshes, topos, Fs, opts)
     setup_s = time.perf_counter() - t0
@@ -328,6 +328,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--F", type=float, default=0.7)
     ap.add_argument("--eta", type=float, default=1e-2)
+    ap.add_argument("--forcing", type=int, default=1, choices=[0, 1],
+                    help="GMRES forcing terms: 0 fixed eta, 1 Eisenstat-Walker (the default of the paper's KINSOL)")
     ap.add_argument("--refine-below", type=float, default=1e-5,
                     help="mixed form: FP32C Newton residuals while |F|inf exceeds this, DF64 after (0: DF64 throughout)")
     ap.add_argument("--precond", default="fp32", choices=["fp32", "fp64"],
@@ -369,7 +371,7 @@ def main():
     mesh, topo, F = W.config_paper_scale(args.F)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=args.eta, precond_precision=_pc_prec(args),
-                               refine_below=args.refine_below)
+                               refine_below=args.refine_below, forcing=args.forcing)
     ctx = bfs.Context(mesh, topo, F, opts)
     pairs_per_residual = ctx.pair_evals
     n_index_pairs = mesh.n_targets * mesh.n_sources
@@ -521,7 +523,8 @@ def main():
     # ---- plain FP64 solve for comparison (not in the timed region) --------
     plain = None
     if not args.no_plain and rank == 0:
-        ctx64 = bfs.Context(mesh, topo, F, bfs.default_options(tol=1e-8))
+        # the same Newton-Krylov settings in FP64 throughout (forcing floor 1e-4)
+        ctx64 = bfs.Context(mesh, topo, F, bfs.default_options(tol=1e-8, forcing=args.forcing))
         ctx64.precond_factor()
         up = ctx64.flat_guess()
         torch.cuda.synchronize()
@@ -599,9 +602,10 @@ def main():
                            "form": "mixed: FP32C residuals inside Jv; Newton residual and line search in "
                                    "double-float (FP64-accurate, 1e-10 per-row parity); FP64 GMRES and "
                                    "banded-LU factorisation; preconditioner sweeps in %s; Newton residuals in "
-                                   "FP32C while |F|inf > %g, double-float after; %s" % (
+                                   "FP32C while |F|inf > %g, double-float after; %s GMRES forcing; %s" % (
                                        "FP32 over FP32 copies of the factors" if args.precond == "fp32" else "FP64",
                                        args.refine_below,
+                                       "Eisenstat-Walker" if args.forcing == 1 else "fixed",
                                        "learned initial guess" if net is not None else "no learned guess"),
                            "l2": "flushed between steps (256 MiB write); sources fit in L2",
                            "parallelism": "replicas" if world > 1 else "single GPU",

@@ -120,6 +120,12 @@ typedef struct {
                               sqrt(1 + |grad zeta|^2)) at the half points (the
                               extension Sec. 6 proposes); the preconditioner gains the
                               linearised term -tau (zeta_xx + zeta_yy).  0 (default). */
+    int forcing;           /* GMRES relative tolerance of Newton step k: 0 (default) the
+                              fixed eta; 1 Eisenstat-Walker choice 1 (the KINSOL
+                              default of Sec. 5's solver), eta_k = | |F_k| - |F_{k-1} +
+                              J s_{k-1}| | / |F_{k-1}|, safeguarded by eta_{k-1}^1.618
+                              when that exceeds 0.1, kept in [eta, 0.9]; eta_0 =
+                              max(eta, 0.1) */
 } bfs_options;
 
 typedef struct {

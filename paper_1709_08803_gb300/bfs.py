@@ -52,7 +52,7 @@ class bfs_options(ctypes.Structure):
                 ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
                 ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int),
                 ("refine_below", ctypes.c_double), ("stall_newton", ctypes.c_int),
-                ("surface_tension", ctypes.c_double)]
+                ("surface_tension", ctypes.c_double), ("forcing", ctypes.c_int)]
 
 
 class bfs_stats(ctypes.Structure):

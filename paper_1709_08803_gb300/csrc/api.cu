@@ -89,6 +89,7 @@ void bfs_default_options(bfs_options *o)
     o->refine_below = 0.0;
     o->stall_newton = 0;
     o->surface_tension = 0.0;
+    o->forcing = 0;
 }
 
 const char *bfs_last_error(const bfs_ctx *c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -124,6 +125,7 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     if (o.krylov_precision != BFS_FP64 && o.krylov_precision != BFS_FP32C && o.krylov_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "unknown krylov_precision");
     if (!(o.refine_below >= 0.0)) return set_err(nullptr, BFS_EINVAL, "refine_below must be >= 0");
+    if (o.forcing != 0 && o.forcing != 1) return set_err(nullptr, BFS_EINVAL, "forcing must be 0 or 1");
     if (!(o.surface_tension >= 0.0) || !isfinite(o.surface_tension))
         return set_err(nullptr, BFS_EINVAL, "surface_tension must be finite and >= 0");
     if (o.precond_precision != BFS_FP64 && o.precond_precision != BFS_FP32C)

@@ -343,6 +343,8 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
     std::vector<int> status(B, 1);  // 1 running, else final status
     std::vector<double> f2(B), finf(B), mu(B);
     std::vector<int> stalls(B, 0);
+    // forcing terms per instance (Eisenstat-Walker choice 1 when o.forcing == 1)
+    std::vector<double> eta(B, o.forcing == 1 ? std::max(o.eta, 0.1) : o.eta), prev_f2(B, -1.0), prev_lin(B, 0.0);
     std::vector<int> all(B);
     std::iota(all.begin(), all.end(), 0);
 
@@ -441,7 +443,13 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
             gi.precs = g[i].precs;
             gi.jvs = g[i].jvs;
             g[i] = gi;
-            bfs::gm_start(c, g[i], u[i], c->d_F, cur[i] != o.krylov_precision ? c->d_F32 : c->d_F, f2[i], o.eta,
+            if (o.forcing == 1 && prev_f2[i] > 0.0) {
+                double e = fabs(f2[i] - prev_lin[i]) / prev_f2[i];
+                const double sg = pow(eta[i], 1.6180339887498949);
+                if (sg > 0.1) e = std::max(e, sg);
+                eta[i] = std::min(0.9, std::max(o.eta, e));
+            }
+            bfs::gm_start(c, g[i], u[i], c->d_F, cur[i] != o.krylov_precision ? c->d_F32 : c->d_F, f2[i], eta[i],
                           o.max_krylov, s);
         }
         if ((rc = read_batch(b, act, 8, 1, s))) return rc;
@@ -492,6 +500,8 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
                 bfs_ctx *c = b->c[i];
                 const double t2 = b->h_sc[4 * i], tinf = b->h_sc[4 * i + 1];
                 if (isfinite(t2) && t2 <= (1.0 - 1e-4 * mu[i]) * f2[i]) {
+                    prev_f2[i] = f2[i];
+                    prev_lin[i] = (1.0 - mu[i]) * f2[i] + mu[i] * g[i].res;
                     f2[i] = t2;
                     finf[i] = tinf;
                     cudaMemcpyAsync(u[i], c->d_ut, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s);

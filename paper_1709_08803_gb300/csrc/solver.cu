@@ -716,7 +716,18 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
     if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
     double f2 = c->h_pin[0], finf = c->h_pin[1];
     int stalls = 0;
+    // forcing terms (Eisenstat-Walker choice 1 when opt.forcing == 1)
+    const double eta_min = c->opt.eta;
+    double eta_k = c->opt.forcing == 1 ? std::max(eta_min, 0.1) : eta_min;
+    double prev_f2 = -1.0, prev_lin = 0.0;
     for (int k = 0;; k++) {
+        if (c->opt.forcing == 1 && prev_f2 > 0.0) {
+            const double prev_eta = eta_k;
+            double e = fabs(f2 - prev_lin) / prev_f2;
+            const double sg = pow(prev_eta, 1.6180339887498949);
+            if (sg > 0.1) e = std::max(e, sg);
+            eta_k = std::min(0.9, std::max(eta_min, e));
+        }
         if (cur != outer && isfinite(finf) && (finf <= c->opt.refine_below || finf <= c->opt.tol)) {
             if ((rc = residual_launch(c, u, c->d_F, outer, s))) return finish(rc);
             count(outer);
@@ -744,7 +755,7 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         Gm gk{};
         gk.precs = g.precs;
         gk.jvs = g.jvs;
-        gm_start(c, gk, u, c->d_F, Fbase, f2, c->opt.eta, c->opt.max_krylov, s);
+        gm_start(c, gk, u, c->d_F, Fbase, f2, eta_k, c->opt.max_krylov, s);
         rc = gmres(c, gk, s);
         S.krylov_its += gk.its;
         g.precs = gk.precs;
@@ -780,6 +791,9 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             mu *= 0.5;
         }
         if (!ok) return finish(BFS_ELINESEARCH);
+        // |F + J (mu du)| estimated from the GMRES residual of the full step
+        prev_f2 = f2;
+        prev_lin = (1.0 - mu) * f2 + mu * gk.res;
         f2 = c->h_pin[0];
         finf = c->h_pin[1];
         BFS_CUDA_TRY(c, cudaMemcpyAsync(u, c->d_ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));

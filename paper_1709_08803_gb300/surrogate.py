@@ -238,7 +238,7 @@ def solver_options(tol: float = 1e-8, budget_s: float = 3.0):
     no steady solution; this makes a failed attempt cost ~0.2 s, not seconds)."""
     return bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=1e-2, max_newton=25, max_krylov=80, time_budget_s=budget_s,
-                               precond_precision=bfs.BFS_FP32C, refine_below=1e-5, stall_newton=3)
+                               precond_precision=bfs.BFS_FP32C, refine_below=1e-5, stall_newton=3, forcing=1)
 
 
 def describe(topo_desc) -> dict:

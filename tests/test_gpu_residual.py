@@ -216,7 +216,7 @@ def test_nan_input_is_flagged():
     assert st["status"] == bfs.BFS_ENAN
 
 
-@pytest.mark.parametrize("kprec", ["fp64", "fp32c", "fp32c+df64", "fp32c+df64+refine"])
+@pytest.mark.parametrize("kprec", ["fp64", "fp32c", "fp32c+df64", "fp32c+df64+refine", "fp32c+df64+refine+ew"])
 def test_solve_small_config_matches_oracle(kprec):
     """refine: FP32C Newton residuals while |F| > 1e-5, DF64 after, FP32
     preconditioner sweeps (the bench's mixed form)."""
@@ -227,7 +227,9 @@ def test_solve_small_config_matches_oracle(kprec):
     assert sref["status"] == 0
     prec = bfs.BFS_FP64 if kprec == "fp64" else bfs.BFS_FP32C
     outer = bfs.BFS_DF64 if "df64" in kprec else bfs.BFS_FP64
-    extra = dict(refine_below=1e-5, precond_precision=bfs.BFS_FP32C) if kprec.endswith("refine") else {}
+    extra = dict(refine_below=1e-5, precond_precision=bfs.BFS_FP32C) if "refine" in kprec else {}
+    if kprec.endswith("ew"):  # Eisenstat-Walker forcing terms
+        extra["forcing"] = 1
     ctx = _ctx(mesh, topo, F, tol=1e-11, krylov_precision=prec, outer_precision=outer,
                eta=1e-4 if kprec == "fp64" else 1e-2, **extra)
     u = ctx.flat_guess()
