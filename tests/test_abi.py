@@ -43,6 +43,9 @@ def test_default_options(L):
     o = bfs.default_options()
     assert o.n_rad == 0.05 and o.sign_I4 == -1.0 and o.tol == 1e-8
     assert o.gmres_restart == 50 and o.krylov_precision == bfs.BFS_FP64
+    # the fields appended later: also checks that the ctypes layout matches the C struct
+    assert o.outer_precision == bfs.BFS_FP64 and o.precond_precision == bfs.BFS_FP64
+    assert o.refine_below == 0.0 and o.stall_newton == 0 and o.surface_tension == 0.0 and o.forcing == 0
 
 
 def _setup(mesh, topo, F, opts=None):
@@ -56,7 +59,8 @@ def _setup(mesh, topo, F, opts=None):
     return rc, ctx
 
 
-@pytest.mark.parametrize("case", ["N", "M", "dx", "F", "half_y1", "beta_pierces", "nan", "restart", "sign"])
+@pytest.mark.parametrize("case", ["N", "M", "dx", "F", "half_y1", "beta_pierces", "nan", "restart", "sign",
+                                  "tension", "refine", "forcing", "precond_precision", "outer_precision"])
 def test_setup_rejects_invalid_input(L, case):
     mesh = W.mesh_box(9, 5, 0.4, 0.4)
     topo = W.gaussian_bumps(mesh, [(0.1, 0.7, 0.0, 0.0)])
@@ -83,6 +87,16 @@ def test_setup_rejects_invalid_input(L, case):
         opts = bfs.default_options(gmres_restart=0)
     elif case == "sign":
         opts = bfs.default_options(sign_I4=0.5)
+    elif case == "tension":
+        opts = bfs.default_options(surface_tension=-0.1)
+    elif case == "refine":
+        opts = bfs.default_options(refine_below=-1.0)
+    elif case == "forcing":
+        opts = bfs.default_options(forcing=2)
+    elif case == "precond_precision":
+        opts = bfs.default_options(precond_precision=bfs.BFS_DF64)
+    elif case == "outer_precision":
+        opts = bfs.default_options(outer_precision=bfs.BFS_FP32C)
     rc, ctx = _setup(mesh, topo, F, opts)
     assert rc == bfs.BFS_EINVAL and not ctx.value
     assert bfs.lib().bfs_last_error(None)
@@ -93,3 +107,16 @@ def test_null_arguments_are_rejected(L):
     assert L.bfs_solve(None, None, None, None) == bfs.BFS_EINVAL
     assert L.bfs_precond_apply(None, None, None, None) == bfs.BFS_EINVAL
     L.bfs_destroy(None)
+
+
+def test_tall_bump_below_the_bernoulli_bound_is_accepted(L):
+    """A bottom above z = 0 is valid as long as it stays below F^2/2 (the
+    supercritical runs of Sec. 5.2): validation passes, so the call gets as
+    far as the device (it fails with BFS_ECUDA only where there is no GPU)."""
+    mesh = W.mesh_box(9, 5, 0.4, 0.4)
+    F = 3.0
+    topo = W.gaussian_bumps(mesh, [(1.5, 0.7, 0.0, 0.0)])  # top at z = 0.5 < F^2/2 = 4.5
+    rc, ctx = _setup(mesh, topo, F, None)
+    assert rc in (bfs.BFS_OK, bfs.BFS_ECUDA, bfs.BFS_ENOMEM)
+    if rc == bfs.BFS_OK:
+        L.bfs_destroy(ctx)
