@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "JFNK solve time & residual pair-evals/s at 181x61, mixed+learned vs plain FP64"
 UNIT = "pair-evals/s"
 # algorithmic work of the FP32C pair kernel per (target half point, source node)
-# index pair: 46 FP32 ALU instructions + 5 MUFU rsqrt = 51 issue slots (see DESIGN.md)
+# index pair: 46 FP32 ALU instructions + 5 MUFU rsqrt = 51 issue slots
 INSTR_PER_INDEX_PAIR = 51
 
 
@@ -547,7 +547,7 @@ def main():
     roofline_pairs = {"bound": "alu", "kernel": "k_pairs<float> (FP32C all-pairs quadrature)",
                 "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
                 "frac": (achieved / peak_tinst) if achieved else None,
-                # dram bytes read + written per launch, ncu (profiles/k_pairs_181x61.md)
+                # dram bytes read + written per launch, from an ncu capture of this kernel at 181x61
                 "traffic": 1.43e6 if args.F == 0.7 else None,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz (max SM clock, {src} peaks file)",
                 "avg_launch_ms": avg32, "launches": n32,
@@ -569,7 +569,7 @@ def main():
                       "us_per_sweep_step": avg_ap * 1e3 / (2 * mesh.M) if nap else None,
                       "achieved": apply_bytes / (avg_ap / 1e3) / 1e9 if nap else None, "peak": hbm,
                       "unit": "GB/s", "frac": (apply_bytes / (avg_ap / 1e3) / 1e9) / hbm if nap else None,
-                      # dram bytes read + written per launch, ncu (profiles/k_apply_tma_181x61.md)
+                      # dram bytes read + written per launch, from an ncu capture of this kernel at 181x61
                       "traffic": 501.1e6 if (esz == 4 and args.F == 0.7) else None,
                       "algorithmic_bytes": apply_bytes, "avg_launch_ms": avg_ap,
                       "launches": nap, "peak_source": f"hbm_gbs of the {src} peaks file",

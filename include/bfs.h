@@ -254,7 +254,7 @@ int bfs_bottom_pressure(bfs_ctx *ctx, const double *u, double *p, double *force_
 int bfs_profile_enable(bfs_ctx *ctx, int on);
 int bfs_profile_read(bfs_ctx *ctx, double *out8, unsigned long long *launches);
 
-/* Batched sweeps (spec extension; the paper solves one problem at a
+/* Batched sweeps (an addition: the paper solves one problem at a
    time).  A batch holds B independent problems -- each its own mesh, bottom
    and Froude number -- and evaluates the FP32C residuals that their Krylov
    iterations need in ONE persistent-kernel launch per step: CTAs take

@@ -1,5 +1,5 @@
 // Learned initial guess: a small convolutional neural operator on the nodal
-// grid (spec extension; the paper starts Newton from a flat surface or
+// grid (an addition: the paper starts Newton from a flat surface or
 // from a nearby solution).  It maps the bottom B = beta + 1, the Froude number
 // and the node coordinates to the nodal fields zeta, phi - x and psi - x; the
 // guess is accepted only through Newton to the same residual tolerance.

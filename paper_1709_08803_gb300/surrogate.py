@@ -1,4 +1,4 @@
-"""Learned initial guess for the JFNK solve (spec extension).
+"""Learned initial guess for the JFNK solve (an addition; the paper has none).
 
 A small convolutional neural operator (the CUDA kernels behind bfs_cno_* in
 csrc/cno.cu: four dilated 3x3 convolutions, BF16 tensor-core contractions with
