@@ -541,3 +541,27 @@ def test_surface_tension_term_is_the_mean_curvature(half):
         errs.append(np.abs(got - kap).max() / np.abs(kap).max())
     assert errs[1] < 1e-2, errs
     assert errs[0] / errs[1] > 3.0, errs  # second order
+
+
+# ---------------------------------------------------------------------------
+# P10: preconditioning with the linear Jacobian clusters the spectrum at 1
+# (Sec. 4.2, eigenvalue figure: a Gaussian bump eps = 0.1, F = 0.6,
+# dx = dy = 0.8, flat-surface iterate; 15 x 15 here instead of 31 x 31).
+# ---------------------------------------------------------------------------
+def test_linear_preconditioner_clusters_the_spectrum():
+    N, dx = 15, 0.8
+    mesh = W.Mesh(N=N, M=N, x1=-0.28 * (N - 1) * dx, y1=-0.5 * (N - 1) * dx, dx=dx, dy=dx)
+    topo = W.gaussian_bumps(mesh, [(0.1, 1 / math.sqrt(2), 0.0, 0.0)])
+    P = O.problem(mesh, 0.6)
+    J = O.fd_jacobian(P, topo, W.flat_guess(mesh))
+    ev = np.linalg.eigvals(J)
+    # unpreconditioned: spread over two decades, almost nothing near 1
+    assert np.abs(ev).max() / np.abs(ev).min() > 20
+    assert np.mean(np.abs(ev - 1) < 0.1) < 0.05
+    # J J~^-1: every eigenvalue within 0.1 of 1
+    evp = np.linalg.eigvals(J @ np.linalg.inv(O.jtilde(P)))
+    assert np.abs(evp - 1).max() < 0.1
+    # the banded preconditioner of App. A keeps most of the cluster
+    for hb in (1, 3):
+        evb = np.linalg.eigvals(J @ np.linalg.inv(O.jtilde(P, half_band=hb)))
+        assert np.mean(np.abs(evb - 1) < 0.1) > 0.9
