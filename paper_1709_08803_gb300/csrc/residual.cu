@@ -305,8 +305,9 @@ k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int
 // Closed-form integral of S2 = (A s^2 + B s t + C t^2)^(-1/2) over a rectangle
 // (Sec. 3.1).  The antiderivative printed in the paper is
 //   t/sqrt(A) ln(2As + Bt + 2 sqrt(A Q)) + s/sqrt(C) ln(2Ct + Bs + 2 sqrt(C Q));
-// where the log argument would cancel (2As + Bt < 0) it is evaluated as
-// ln((4AC - B^2) t^2) - ln(2 sqrt(AQ) - 2As - Bt), and t ln(.) -> 0 at t = 0.
+// where the log argument would cancel (2As + Bt < 0) it is evaluated through
+// (2As + Bt + 2 sqrt(AQ)) (2 sqrt(AQ) - 2As - Bt) = (4AC - B^2) t^2 as
+// ln((4AC - B^2) t^2 / (2 sqrt(AQ) - 2As - Bt)), and t ln(.) -> 0 at t = 0.
 // ---------------------------------------------------------------------------
 __device__ double antideriv_S2(double A, double B, double C, double s, double t)
 {
@@ -315,12 +316,13 @@ __device__ double antideriv_S2(double A, double B, double C, double s, double t)
     double g = 0.0;
     if (t != 0.0) {
         const double lin = 2.0 * A * s + B * t, r = 2.0 * sqrt(A * Q);
-        const double L = (lin >= 0.0) ? log(lin + r) : (log(D * t * t) - log(r - lin));
+        // lin + r = D t^2 / (r - lin): one logarithm, no cancellation when lin < 0
+        const double L = log((lin >= 0.0) ? lin + r : D * t * t / (r - lin));
         g += t * rsqrt(A) * L;
     }
     if (s != 0.0) {
         const double lin = 2.0 * C * t + B * s, r = 2.0 * sqrt(C * Q);
-        const double L = (lin >= 0.0) ? log(lin + r) : (log(D * s * s) - log(r - lin));
+        const double L = log((lin >= 0.0) ? lin + r : D * s * s / (r - lin));
         g += s * rsqrt(C) * L;
     }
     return g;
