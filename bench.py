@@ -102,6 +102,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def replica_rate(seconds: float, evals: float, pairs_per_residual: float, dist=None, device: str = "cpu"):
+    """Whole-job rate of N independent replicas (one per rank): every rank's
+    pair evaluations over the slowest rank's time.  Returns (rate, slowest
+    seconds).  With dist (an initialised torch.distributed) the time is the
+    max over ranks; every rank gets the same answer."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    total = float(seconds)
+    if dist:
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+        dist.barrier()
+    return world * evals * pairs_per_residual / total, total
+
+
 def cpu_oracle_rate(mesh, topo, F, u, reps: int = 1):
     import oracle as O
     P = O.problem(mesh, F)
@@ -477,13 +493,7 @@ def main():
     ctx.profile_enable(False)
     (ms64, n64), (ms32, n32), (msdf, ndf) = prof["fp64"], prof["fp32c"], prof["df64"]
     msap, nap = prof["apply"]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        dist.barrier()
-    value = world * evals * pairs_per_residual / total_s
+    value, total_s = replica_rate(sum(step_ms) / 1e3, evals, pairs_per_residual, dist, "cuda")
     ms_per_step = total_s * 1e3 / args.steps
     status_ok = all(s["status"] == 0 for s in stats)
 
@@ -518,7 +528,7 @@ def main():
             e2e_times.append(time.perf_counter() - t0)
             e2e_evals += st["residual_evals_fp64"] + st["residual_evals_fp32"]
         e2e_entry = "bfs_solve_host"
-    e2e_value = world * e2e_evals * pairs_per_residual / sum(e2e_times)
+    e2e_value, _ = replica_rate(sum(e2e_times), e2e_evals, pairs_per_residual, dist, "cuda")
 
     # ---- plain FP64 solve for comparison (not in the timed region) --------
     plain = None
