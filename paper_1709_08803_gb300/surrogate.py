@@ -164,18 +164,6 @@ def features(mesh, topo, F: float) -> np.ndarray:
     return f.astype(np.float32)
 
 
-def sample_problem(rng, mesh):
-    """One draw of the batched-sweep distribution (F, bumps or a ridge) on `mesh`."""
-    F = float(rng.uniform(0.5, 1.4))
-    if rng.uniform() < 0.8:
-        nb = int(rng.integers(1, 4))
-        bumps = [(float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)),
-                  float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2))) for _ in range(nb)]
-        return W.gaussian_bumps(mesh, bumps), F
-    return W.gaussian_bumps(mesh, [], ridges=[(float(rng.uniform(0.05, 0.3)), float(rng.uniform(0.5, 2.0)),
-                                               float(rng.uniform(-2, 2)))]), F
-
-
 def scaled(topo, s: float):
     """The bottom with every bump height multiplied by s (beta + 1 scales linearly)."""
     return W.Topography(-1.0 + s * (topo.beta + 1.0), s * topo.beta_x, s * topo.beta_y)
@@ -250,7 +238,8 @@ def describe(topo_desc) -> dict:
 
 
 def sample_problem_desc(rng, mesh):
-    """sample_problem plus a description of the draw (for the records)."""
+    """One draw of the batched-sweep distribution (F, 1-3 bumps or a ridge) on
+    `mesh`: (topography, F, description of the draw for the records)."""
     F = float(rng.uniform(0.5, 1.4))
     if rng.uniform() < 0.8:
         nb = int(rng.integers(1, 4))
