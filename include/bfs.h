@@ -174,7 +174,9 @@ int bfs_set_surface_pressure(bfs_ctx *ctx, const double *p);
 
 /* Change the Froude number.  The factored preconditioner (formed for the
    previous F) is kept as an approximation and stays usable; call
-   bfs_precond_factor to refresh it.  BFS_EINVAL for F <= 0. */
+   bfs_precond_factor to refresh it.  Synchronous.  BFS_EINVAL, with the
+   context unchanged, for F <= 0 or an F whose F^2/2 the current bottom
+   reaches (the bound bfs_setup checks). */
 int bfs_set_froude(bfs_ctx *ctx, double F);
 const char *bfs_last_error(const bfs_ctx *ctx);
 int bfs_n_unknowns(const bfs_ctx *ctx);

@@ -133,17 +133,20 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     if (o.outer_precision != BFS_FP64 && o.outer_precision != BFS_DF64)
         return set_err(nullptr, BFS_EINVAL, "outer_precision must be BFS_FP64 or BFS_DF64");
     const size_t NM = (size_t)N * M;
+    double beta_max = -INFINITY;
     for (size_t q = 0; q < NM; q++) {
         if (!isfinite(topo->beta[q]) || !isfinite(topo->beta_x[q]) || !isfinite(topo->beta_y[q]))
             return set_err(nullptr, BFS_EINVAL, "topography has a non-finite value");
         if (!(topo->beta[q] < 0.5 * F * F))
             return set_err(nullptr, BFS_EINVAL, "the bottom reaches F^2/2, above any possible free surface");
+        beta_max = std::max(beta_max, topo->beta[q]);
     }
 
     bfs_ctx *c = new (std::nothrow) bfs_ctx();
     if (!c) return set_err(nullptr, BFS_ENOMEM, "host allocation failed");
     c->N = N; c->M = M; c->half = mesh->half_domain ? 1 : 0;
     c->x1 = mesh->x1; c->y1 = mesh->y1; c->dx = mesh->dx; c->dy = mesh->dy; c->F = F;
+    c->beta_max = beta_max;
     c->opt = o;
     c->n = 3 * (N + 1) * M;
     c->Nt = (N - 1) * M;
@@ -205,17 +208,20 @@ int bfs_set_topography(bfs_ctx *c, const bfs_topo *topo)
     if (!c || !topo || !topo->beta || !topo->beta_x || !topo->beta_y)
         return set_err(c, BFS_EINVAL, "NULL argument");
     const size_t NM = (size_t)c->NM;
+    double beta_max = -INFINITY;
     for (size_t q = 0; q < NM; q++) {
         if (!isfinite(topo->beta[q]) || !isfinite(topo->beta_x[q]) || !isfinite(topo->beta_y[q]))
             return set_err(c, BFS_EINVAL, "topography has a non-finite value");
         if (!(topo->beta[q] < 0.5 * c->F * c->F))
             return set_err(c, BFS_EINVAL, "the bottom reaches F^2/2, above any possible free surface");
+        beta_max = std::max(beta_max, topo->beta[q]);
     }
     BFS_CUDA_TRY(c, cudaDeviceSynchronize());
     bfs::gm_graphs_clear(c);
     BFS_CUDA_TRY(c, cudaMemcpy(c->d_beta, topo->beta, sizeof(double) * NM, cudaMemcpyHostToDevice));
     BFS_CUDA_TRY(c, cudaMemcpy(c->d_bx, topo->beta_x, sizeof(double) * NM, cudaMemcpyHostToDevice));
     BFS_CUDA_TRY(c, cudaMemcpy(c->d_by, topo->beta_y, sizeof(double) * NM, cudaMemcpyHostToDevice));
+    c->beta_max = beta_max;
     double *u0 = c->d_Fp;
     k_flat_guess<<<(c->n + 255) / 256, 256>>>(u0, c->N, c->M, c->x1);
     c->launches++;
@@ -249,6 +255,9 @@ int bfs_set_froude(bfs_ctx *c, double F)
 {
     if (!c) return BFS_EINVAL;
     if (!(F > 0.0) || !isfinite(F)) return set_err(c, BFS_EINVAL, "F must be positive");
+    if (!(c->beta_max < 0.5 * F * F))
+        return set_err(c, BFS_EINVAL, "the bottom reaches F^2/2, above any possible free surface");
+    BFS_CUDA_TRY(c, cudaDeviceSynchronize());
     bfs::gm_graphs_clear(c);  // F is an argument of the captured finish kernels
     c->F = F;
     return BFS_OK;

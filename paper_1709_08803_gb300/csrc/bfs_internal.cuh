@@ -64,6 +64,7 @@ struct bfs_ctx {
     // problem
     int N, M, half;
     double x1, y1, dx, dy, F;
+    double beta_max;  // highest bottom node; a valid F keeps it below F^2/2
     bfs_options opt;
     int n, Nt, NM, Ns, Ns_cap;
     double xc, yc;  // centre of the mesh (physical)

@@ -346,6 +346,14 @@ def test_set_topography_and_froude_keep_the_preconditioner():
     assert np.abs(O.residual(O.problem(mesh, 0.75), bigger, u.cpu().numpy())).max() <= 1e-10
     with pytest.raises(bfs.BfsError):
         ctx.set_froude(0.0)
+    # beta is the bottom's height: a bump of 1.1 on the bed at z = -1 tops out at z = 0.1,
+    # which F = 0.7 allows (F^2/2 = 0.245) and F = 0.3 does not (0.045)
+    tall = W.gaussian_bumps(mesh, [(1.1, 1.0 / math.sqrt(2.0), 0.0, 0.0)])
+    assert 0.09 < tall.beta.max() < 0.11
+    ctx2 = _ctx(mesh, tall, 0.7)
+    with pytest.raises(bfs.BfsError):
+        ctx2.set_froude(0.3)
+    ctx2.set_froude(0.5)  # F^2/2 = 0.125 is above the top
 
 
 @pytest.mark.parametrize("name", ["small_half_31x11", "ragged_full_23x9"])
