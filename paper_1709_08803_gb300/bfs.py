@@ -143,6 +143,19 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _require(ok: bool, msg: str):
+    """Argument check that survives python -O: a buffer of the wrong size,
+    type or device would otherwise reach the kernels as a raw pointer."""
+    if not ok:
+        raise ValueError(msg)
+
+
+def _is_f64_cuda(t, n: int | None = None) -> bool:
+    import torch
+    return (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and (n is None or t.numel() == n))
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -188,10 +201,13 @@ class Context:
             pass
 
     def _vec(self, t):
-        import torch
-        assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-        assert t.is_contiguous() and t.numel() == self.n, "expected a contiguous float64 CUDA vector of length n"
+        _require(_is_f64_cuda(t, self.n), f"expected a contiguous float64 CUDA vector of length {self.n}")
         return ctypes.c_void_p(_ptr(t))
+
+    def _host_vec(self, a):
+        _require(isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                 and a.size == self.n, f"expected a contiguous float64 numpy vector of length {self.n}")
+        return ctypes.c_void_p(a.ctypes.data)
 
     # --- the C ABI, one method per entry point -----------------------------
     def residual(self, u, out=None, precision: int = BFS_FP64, stream=None):
@@ -234,21 +250,18 @@ class Context:
         return st.as_dict()
 
     def solve_host(self, u_host: np.ndarray, stream=None, raise_on_error: bool = True):
-        assert u_host.dtype == np.float64 and u_host.flags.c_contiguous and u_host.size == self.n
         st = bfs_stats()
-        rc = lib().bfs_solve_host(self._ctx, ctypes.c_void_p(u_host.ctypes.data), ctypes.byref(st),
-                                  _stream(stream))
+        rc = lib().bfs_solve_host(self._ctx, self._host_vec(u_host), ctypes.byref(st), _stream(stream))
         if raise_on_error:
             self._check(rc)
         return st.as_dict()
 
     def residual_host(self, u_host: np.ndarray, out: np.ndarray | None = None,
                       precision: int = BFS_FP64, stream=None):
-        assert u_host.dtype == np.float64 and u_host.flags.c_contiguous and u_host.size == self.n
         if out is None:
             out = np.empty(self.n)
-        self._check(lib().bfs_residual_host(self._ctx, ctypes.c_void_p(u_host.ctypes.data),
-                                            ctypes.c_void_p(out.ctypes.data), precision, _stream(stream)))
+        self._check(lib().bfs_residual_host(self._ctx, self._host_vec(u_host), self._host_vec(out),
+                                            precision, _stream(stream)))
         return out
 
     def flat_guess(self, out=None, stream=None):
@@ -278,7 +291,7 @@ class Context:
             self._check(lib().bfs_set_surface_pressure(self._ctx, None))
             return
         self._p = np.ascontiguousarray(p, dtype=np.float64).ravel()
-        assert self._p.size == self.mesh.N * self.mesh.M
+        _require(self._p.size == self.mesh.N * self.mesh.M, "p needs one value per node (N*M)")
         self._check(lib().bfs_set_surface_pressure(self._ctx, ctypes.c_void_p(self._p.ctypes.data)))
 
     def set_froude(self, F: float):
@@ -312,8 +325,12 @@ def residual_static(mesh, beta, beta_x, beta_y, F: float, u, out=None, precision
     import torch
     if out is None:
         out = torch.empty_like(u)
-    for t in (beta, beta_x, beta_y, u, out):
-        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    NM = mesh.N * mesh.M
+    for t in (beta, beta_x, beta_y):
+        _require(_is_f64_cuda(t, NM), f"beta, beta_x, beta_y: contiguous float64 CUDA arrays of N*M = {NM}")
+    n = 3 * (mesh.N + 1) * mesh.M
+    for t in (u, out):
+        _require(_is_f64_cuda(t, n), f"u, out: contiguous float64 CUDA vectors of length {n}")
     m = bfs_mesh(mesh.N, mesh.M, int(mesh.half), mesh.x1, mesh.y1, mesh.dx, mesh.dy)
     rc = lib().bfs_residual_static(ctypes.byref(m), ctypes.c_void_p(_ptr(beta)), ctypes.c_void_p(_ptr(beta_x)),
                                    ctypes.c_void_p(_ptr(beta_y)), float(F), float(n_rad), float(sign_I4),
@@ -332,7 +349,7 @@ class Batch:
         if not torch.cuda.is_available():
             raise RuntimeError("CUDA device required: libbfs has no CPU path")
         B = len(meshes)
-        assert len(topos) == B and len(Fs) == B
+        _require(len(topos) == B and len(Fs) == B, "meshes, topos and Fs differ in length")
         self.meshes = list(meshes)
         D = ctypes.POINTER(ctypes.c_double)
         self._h = []
@@ -370,10 +387,9 @@ class Batch:
             pass
 
     def _ptrs(self, ts):
-        import torch
-        assert len(ts) == self.B
-        for t, n in zip(ts, self.n):
-            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n
+        _require(len(ts) == self.B, f"expected {self.B} vectors")
+        for i, (t, n) in enumerate(zip(ts, self.n)):
+            _require(_is_f64_cuda(t, n), f"vector {i}: expected a contiguous float64 CUDA vector of length {n}")
         return (_VP * self.B)(*[_ptr(t) for t in ts])
 
     def flat_guesses(self):
@@ -396,6 +412,8 @@ class Batch:
 
     def instance_residual(self, i, u, precision: int = BFS_FP64, stream=None):
         import torch
+        _require(0 <= i < self.B, f"instance {i} is not in the batch")
+        _require(_is_f64_cuda(u, self.n[i]), f"instance {i}: expected a contiguous float64 CUDA vector of length {self.n[i]}")
         out = torch.empty_like(u)
         self._check(lib().bfs_residual(lib().bfs_batch_instance(self._b, i), ctypes.c_void_p(_ptr(u)),
                                        ctypes.c_void_p(_ptr(out)), precision, _stream(stream)))

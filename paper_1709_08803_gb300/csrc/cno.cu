@@ -1,6 +1,6 @@
-// Learned initial guess: a small convolutional neural operator on the nodal
-// grid (an addition: the paper starts Newton from a flat surface or
-// from a nearby solution).  It maps the bottom B = beta + 1, the Froude number
+// Learned initial guess (C ABI in include/bfs_cno.h): a small convolutional
+// neural operator on the nodal grid (an addition: the paper starts Newton from
+// a flat surface or from a nearby solution).  It maps the bottom B = beta + 1, the Froude number
 // and the node coordinates to the nodal fields zeta, phi - x and psi - x; the
 // guess is accepted only through Newton to the same residual tolerance.
 //
@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "bfs_cno.h"
 #include "bfs_internal.cuh"
 
 namespace {

@@ -105,11 +105,24 @@ class CNO:
         except Exception:
             pass
 
+    def _images(self, x, ch: int, Bt: int | None = None) -> int:
+        """Checks x is a contiguous float32 CUDA tensor [Bt][H][W][ch] with
+        1 <= Bt <= batch_max (and Bt as given); returns Bt."""
+        import torch
+        bfs._require(isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32
+                     and x.is_contiguous() and x.dim() == 4 and tuple(x.shape[1:]) == (self.H, self.W, ch),
+                     f"expected a contiguous float32 CUDA tensor [Bt, {self.H}, {self.W}, {ch}]")
+        n = int(x.shape[0])
+        bfs._require(1 <= n <= self.batch_max and (Bt is None or n == Bt),
+                     f"batch of {n} images (at most {self.batch_max}, matching the inputs)")
+        return n
+
     def set_params(self, p: np.ndarray, scale=None):
-        p = np.ascontiguousarray(p, dtype=np.float32)
-        assert p.size == self.np
+        p = np.ascontiguousarray(p, dtype=np.float32).ravel()
+        bfs._require(p.size == self.np, f"expected {self.np} parameters")
         if scale is not None:
-            self.scale = np.ascontiguousarray(scale, dtype=np.float32)
+            self.scale = np.ascontiguousarray(scale, dtype=np.float32).ravel()
+            bfs._require(self.scale.size == 3, "expected 3 output scales")
         F = ctypes.POINTER(ctypes.c_float)
         self._check(_lib().bfs_cno_set_params(self._n, p.ctypes.data_as(F), self.scale.ctypes.data_as(F)))
 
@@ -121,12 +134,13 @@ class CNO:
     def forward(self, x):
         """x: CUDA float32 [Bt, H, W, 4] -> CUDA float32 [Bt, H, W, 16]."""
         import torch
-        Bt = x.shape[0]
+        Bt = self._images(x, 4)
         y = torch.empty((Bt, self.H, self.W, 16), dtype=torch.float32, device="cuda")
         self._check(_lib().bfs_cno_forward(self._n, _VP(x.data_ptr()), Bt, _VP(y.data_ptr()), bfs._stream(None)))
         return y
 
     def gradient(self, x, t):
+        self._images(t, 3, self._images(x, 4))
         g = np.empty(self.np, dtype=np.float32)
         loss = ctypes.c_float()
         F = ctypes.POINTER(ctypes.c_float)
@@ -135,6 +149,7 @@ class CNO:
         return g, loss.value
 
     def train_step(self, x, t, lr: float):
+        self._images(t, 3, self._images(x, 4))
         self._check(_lib().bfs_cno_train_step(self._n, _VP(x.data_ptr()), _VP(t.data_ptr()), x.shape[0],
                                               float(lr), bfs._stream(None)))
 
@@ -146,9 +161,10 @@ class CNO:
     def guess(self, ctx: bfs.Context, x, u=None):
         """Unknown vector for ctx from features x (CUDA float32 [1, M, N, 4])."""
         import torch
+        self._images(x, 4, 1)
         if u is None:
             u = torch.empty(ctx.n, dtype=torch.float64, device="cuda")
-        self._check(_lib().bfs_cno_guess(self._n, ctx._ctx, _VP(x.data_ptr()), _VP(u.data_ptr()),
+        self._check(_lib().bfs_cno_guess(self._n, ctx._ctx, _VP(x.data_ptr()), ctx._vec(u),
                                          bfs._stream(None)))
         return u
 

@@ -4,6 +4,7 @@ any device work."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -12,7 +13,8 @@ from paper_1709_08803_gb300 import build as B
 from paper_1709_08803_gb300 import bfs
 from paper_1709_08803_gb300 import workloads as W
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bfs.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADERS = sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -22,16 +24,30 @@ def L():
 
 
 def declared():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(bfs_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(bfs_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared()
     for must in ("bfs_setup", "bfs_residual", "bfs_jvp", "bfs_precond_factor", "bfs_precond_apply",
-                 "bfs_solve", "bfs_destroy", "bfs_last_error"):
+                 "bfs_solve", "bfs_destroy", "bfs_last_error", "bfs_cno_create", "bfs_cno_guess"):
         assert must in names
+
+
+def test_every_exported_entry_point_is_declared(L):
+    """The other direction: no bfs_* function leaves the library undocumented."""
+    nm = subprocess.run(["nm", "-D", "--defined-only", bfs.LIB_PATH], capture_output=True, text=True)
+    if nm.returncode != 0:
+        pytest.skip("nm unavailable")
+    exported = {ln.split()[-1] for ln in nm.stdout.splitlines()
+                if len(ln.split()) == 3 and ln.split()[1] == "T" and ln.split()[-1].startswith("bfs_")}
+    assert exported, "no bfs_ symbols exported"
+    missing = sorted(exported - set(declared()))
+    assert not missing, missing
 
 
 def test_every_declared_symbol_is_exported(L):
