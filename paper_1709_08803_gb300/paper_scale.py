@@ -7,40 +7,102 @@ bump height, the paper's route to its large-amplitude solutions.
 Each stage starts from the previous stage's solution; the preconditioner is
 factored once (it does not depend on the bottom, Sec. 4.2).  Reported per
 stage: Newton and Krylov iterations, residual evaluations, wall time, the
-final residual and the maximum surface height (the quantity Sec. 5 prints:
-2.556 for eps = 2.75 in the supercritical case).  Everything runs in the
-library's kernels; this module only sequences the calls.
+final residual, the maximum surface height (the quantity Sec. 5 prints:
+2.556 for eps = 2.75 in the supercritical case) and, for supercritical flow,
+the apparent wake angle and the wave steepness of Sec. 5.2 (Fig. 6).  The
+solve runs in the library's kernels; this module sequences the calls and
+post-processes the downloaded surface (wake_metrics).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import sys
 import time
 
 import numpy as np
 
 
-def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: int = 40, log=print):
+def wake_metrics(x, y, zeta, zeta_x, zeta_y, x_from: float = 15.0, x_to: float = 45.0):
+    """Apparent wake angle and wave steepness of a supercritical wave pattern
+    (Sec. 5.2, Fig. 6): the angle between the main V-shaped ridge and the
+    centreline, and the maximum slope of the surface on the outside of that
+    ridge.  The default columns, 15 <= x <= 45 on the 281 x 281 mesh of
+    Sec. 5.2, start five bump widths downstream (the ridge is still curved
+    nearer the bump) and stop six units short of the downstream edge.
+
+    x (N,), y (M,): node coordinates; zeta, zeta_x, zeta_y: nodal fields
+    [M, N] (row j at y[j]).  In every column with x_from <= x <= x_to the
+    ridge is the crest of largest height on each side of the centreline,
+    located to sub-node accuracy by the parabola through the crest node and
+    its two neighbours; a least-squares line y = a + b x through the crests
+    of each side gives the angle atan(b).  The steepness is the largest
+    |grad zeta| over the nodes of those columns lying farther from the
+    centreline than the ridge.  Returns a dict with the angle in degrees
+    (mean of the two sides), both sides' angles, the steepness and the rms
+    distance of the crests from the fitted lines."""
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    zeta, zeta_x, zeta_y = (np.asarray(a, float) for a in (zeta, zeta_x, zeta_y))
+    cols = np.nonzero((x >= x_from) & (x <= x_to))[0]
+    if cols.size < 2:
+        raise ValueError("fewer than two columns between x_from and x_to")
+    dy = y[1] - y[0]
+    angles, rms, steep = [], [], 0.0
+    slope = np.hypot(zeta_x, zeta_y)
+    for side in (1.0, -1.0):
+        rows = np.nonzero(side * y > 0.0)[0]
+        if rows.size < 3:
+            raise ValueError("fewer than three rows on a side of the centreline")
+        yr = np.empty(cols.size)
+        for k, i in enumerate(cols):
+            col = zeta[rows, i]
+            m = int(np.argmax(col))
+            off = 0.0
+            if 0 < m < rows.size - 1:
+                a, b, c = col[m - 1], col[m], col[m + 1]
+                den = a - 2.0 * b + c
+                if den < 0.0:
+                    off = 0.5 * (a - c) / den
+            yr[k] = y[rows[m]] + off * dy * (1.0 if rows[1] > rows[0] else -1.0)
+        b, a = np.polyfit(x[cols], side * yr, 1)
+        angles.append(math.degrees(math.atan(b)))
+        rms.append(float(np.sqrt(np.mean((side * yr - (a + b * x[cols])) ** 2))))
+        for k, i in enumerate(cols):
+            outside = rows[side * y[rows] > side * yr[k]]
+            if outside.size:
+                steep = max(steep, float(slope[outside, i].max()))
+    return {"wake_angle_deg": float(np.mean(angles)), "wake_angle_sides_deg": angles,
+            "steepness": steep, "ridge_fit_rms": max(rms)}
+
+
+def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: int = 40, log=print,
+        F: float | None = None, on_stage=None):
     import torch
 
     from . import bfs
     from . import workloads as W
 
-    cfg = W.config_supercritical_281 if case == "super" else W.config_subcritical_281
-    mesh, topo, F = cfg(eps_list[0])
+    if case == "super":
+        def cfg(e):
+            return W.config_supercritical_281(e, 3.0 if F is None else F)
+    else:
+        cfg = W.config_subcritical_281
+    mesh, topo, F0 = cfg(eps_list[0])
     opts = bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=1e-2, max_newton=max_newton, max_krylov=400, refine_below=1e-5,
                                precond_precision=bfs.BFS_FP32C, half_band=half_band)
-    ctx = bfs.Context(mesh, topo, F, opts)
+    ctx = bfs.Context(mesh, topo, F0, opts)
     t0 = time.perf_counter()
     ctx.precond_factor()
     torch.cuda.synchronize()
     factor_s = time.perf_counter() - t0
-    log(f"{case} 281x281: {ctx.n} unknowns, {ctx.pair_evals:.3e} pair evaluations per residual, "
+    log(f"{case} 281x281 F={F0}: {ctx.n} unknowns, {ctx.pair_evals:.3e} pair evaluations per residual, "
         f"preconditioner (half band {half_band}) factored in {factor_s:.1f} s")
     u = ctx.flat_guess()
     stages = []
+    rep = {"case": case, "mesh": "281x281", "F": F0, "half_band": half_band, "factor_s": factor_s,
+           "unknowns": mesh.n_unknowns, "pair_evals_per_residual": mesh.pair_evals(), "stages": stages}
     for eps in eps_list:
         _, topo_e, _ = cfg(eps)
         ctx.set_topography(topo_e)
@@ -49,37 +111,60 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
         st = ctx.solve(u, raise_on_error=False)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
-        nv = ctx.unpack(u)
-        z = nv["zeta"].cpu().numpy()
+        nv = {k: v.cpu().numpy() for k, v in ctx.unpack(u).items()}
+        z = nv["zeta"]
         jc = int(np.argmin(np.abs(mesh.y())))
         rec = {"eps": eps, "status": st["status"], "newton": st["newton_its"], "krylov": st["krylov_its"],
                "evals_fp32c": st["residual_evals_fp32"], "evals_fp64": st["residual_evals_fp64"],
                "fnorm_inf": st["fnorm_inf"], "seconds": secs, "zeta_max": float(z.max()),
                "zeta_min": float(z.min()), "centreline_max": float(z[jc].max())}
+        if case == "super" and st["status"] == 0:
+            rec.update(wake_metrics(mesh.x(), mesh.y(), z, nv["zeta_x"], nv["zeta_y"]))
         stages.append(rec)
         log(json.dumps(rec))
+        if on_stage:
+            on_stage(rep, eps, nv)
         if st["status"] != 0:
             break
     ctx.close()
-    return {"case": case, "mesh": "281x281", "F": F, "half_band": half_band, "factor_s": factor_s,
-            "unknowns": mesh.n_unknowns, "pair_evals_per_residual": mesh.pair_evals(), "stages": stages}
+    return rep
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="super", choices=["super", "sub"])
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1, 0.5, 1.0, 1.5, 2.0, 2.5, 2.75])
+    ap.add_argument("--F", type=float, default=None, help="Froude number of the supercritical case (3)")
     ap.add_argument("--half-band", type=int, default=3)
     ap.add_argument("--max-newton", type=int, default=40)
-    ap.add_argument("--out", default=None)
+    ap.add_argument("--out", default=None, help="report (JSON), rewritten after every stage")
+    ap.add_argument("--fields", default=None, help="surface fields of every converged stage (.npz)")
+    ap.add_argument("--analyse", default=None,
+                    help="recompute the wake metrics from a --fields file of a supercritical run (no GPU)")
     a = ap.parse_args(argv)
+    if a.analyse:
+        from . import workloads as W
+        mesh, _, _ = W.config_supercritical_281(0.1, 3.0 if a.F is None else a.F)
+        d = np.load(a.analyse)
+        for eps in sorted(float(k[len("zeta_eps"):]) for k in d.files if k.startswith("zeta_eps")):
+            m = wake_metrics(mesh.x(), mesh.y(), *(d[f"{k}_eps{eps:g}"] for k in ("zeta", "zeta_x", "zeta_y")))
+            print(json.dumps({"eps": eps, "zeta_max": float(d[f"zeta_eps{eps:g}"].max()), **m}))
+        return 0
     import __graft_entry__
     __graft_entry__.build()
+    saved = {}
+
+    def on_stage(rep, eps, nv):
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(rep, fh, indent=1)
+        if a.fields and rep["stages"][-1]["status"] == 0:
+            for k in ("zeta", "zeta_x", "zeta_y"):
+                saved[f"{k}_eps{eps:g}"] = nv[k]
+            np.savez_compressed(a.fields, **saved)
+
     rep = run(a.case, a.eps, a.half_band, max_newton=a.max_newton,
-              log=lambda m: print(m, file=sys.stderr, flush=True))
-    if a.out:
-        with open(a.out, "w") as fh:
-            json.dump(rep, fh, indent=1)
+              log=lambda m: print(m, file=sys.stderr, flush=True), F=a.F, on_stage=on_stage)
     print(json.dumps(rep))
     return 0
 

@@ -159,13 +159,14 @@ def config_large():
     return mesh, topo, 0.9
 
 
-def config_supercritical_281(eps: float = 0.1):
-    """The paper's supercritical runs (Sec. 5.2, Fig. 5): 281 x 281 nodes,
-    x in [-21, 51], y in [-36, 36] (dx = dy = 72/280 = 0.257), F = 3, one
-    Gaussian bump of width delta = 3 at the origin with height eps."""
+def config_supercritical_281(eps: float = 0.1, F: float = 3.0):
+    """The paper's supercritical runs (Sec. 5.2, Figs. 5-6): 281 x 281 nodes,
+    x in [-21, 51], y in [-36, 36] (dx = dy = 72/280 = 0.257), F = 3 (Fig. 6
+    also F = 4), one Gaussian bump of width delta = 3 at the origin with
+    height eps."""
     h = 72.0 / 280.0
     mesh = Mesh(N=281, M=281, x1=-21.0, y1=-36.0, dx=h, dy=h, half=0)
-    return mesh, gaussian_bumps(mesh, [(eps, 3.0, 0.0, 0.0)]), 3.0
+    return mesh, gaussian_bumps(mesh, [(eps, 3.0, 0.0, 0.0)]), float(F)
 
 
 def config_subcritical_281(eps: float = 0.1):
