@@ -130,9 +130,99 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
     return rep
 
 
+def wave_heights(x, y, zeta, zeta_x, zeta_y, x_from: float = 5.0, x_to: float = 15.0):
+    """Transverse and divergent wave heights of a subcritical wake (Sec. 6,
+    Fig. 11), downstream over x_from <= x <= x_to: the transverse height is
+    half the crest-to-trough range of zeta on the centreline; the divergent
+    height is the highest crest in the sector 12 to 25 degrees off the
+    centreline (around the 19.47-degree Kelvin wedge edge, where the divergent
+    crests meet the transverse ones); the steepness is the largest |grad zeta|
+    in the whole downstream strip."""
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    zeta = np.asarray(zeta, float)
+    cols = (x >= x_from) & (x <= x_to)
+    jc = int(np.argmin(np.abs(y)))
+    centre = zeta[jc, cols]
+    X, Y = np.meshgrid(x, y)
+    ang = np.degrees(np.arctan2(np.abs(Y), np.maximum(X, 1e-12)))
+    sector = (X >= x_from) & (X <= x_to) & (ang >= 12.0) & (ang <= 25.0)
+    strip = (X >= x_from) & (X <= x_to)
+    return {"transverse_height": float(0.5 * (centre.max() - centre.min())),
+            "divergent_crest": float(zeta[sector].max()),
+            "downstream_steepness": float(np.hypot(zeta_x, zeta_y)[strip].max())}
+
+
+def compare_bump_pressure(eps: float = 0.285, half_band: int = 3, tol: float = 1e-8, max_newton: int = 40,
+                          log=print, on_case=None, linear_check: bool = True):
+    """Sec. 6, Fig. 11: flow at F = 0.6 over the Gaussian bump (delta = 0.5,
+    height eps) and past the applied pressure that gives the same linear wake
+    (workloads.gaussian_equivalent_pressure), on the 281 x 281 mesh of
+    Sec. 5.1.  One context and one factorisation serve both problems (the
+    linear Jacobian depends on neither the bottom nor the pressure, Sec. 4.2).
+    Per problem: the solve's counts and wave heights; for the pair, the
+    largest departure from the linear relation zeta_bump = zeta_pressure +
+    F^2 p relative to the largest bump wave (zero in the linear limit).  With
+    linear_check the pair is solved again at eps / 10, where the relation
+    should nearly hold."""
+    import torch
+
+    from . import bfs
+    from . import workloads as W
+
+    mesh, topo_b, F = W.config_subcritical_281(eps)
+    opts = bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
+                               eta=1e-2, max_newton=max_newton, max_krylov=400, refine_below=1e-5,
+                               precond_precision=bfs.BFS_FP32C, half_band=half_band)
+    ctx = bfs.Context(mesh, topo_b, F, opts)
+    t0 = time.perf_counter()
+    ctx.precond_factor()
+    torch.cuda.synchronize()
+    rep = {"case": "bump_vs_pressure", "mesh": "281x281", "F": F, "delta": 0.5,
+           "factor_s": time.perf_counter() - t0, "pairs": []}
+    log(f"bump vs pressure 281x281 F={F}: preconditioner factored in {rep['factor_s']:.1f} s")
+    for e in ([eps, eps / 10.0] if linear_check else [eps]):
+        pair = {"eps": e}
+        fields = {}
+        for kind in ("bump", "pressure"):
+            if kind == "bump":
+                ctx.set_surface_pressure(None)
+                ctx.set_topography(W.config_subcritical_281(e)[1])
+            else:
+                ctx.set_topography(W.flat_topography(mesh))
+                p = W.gaussian_equivalent_pressure(mesh, e, 0.5, F)
+                ctx.set_surface_pressure(p)
+            u = ctx.flat_guess()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.solve(u, raise_on_error=False)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            nv = {k: v.cpu().numpy() for k, v in ctx.unpack(u).items()}
+            rec = {"status": st["status"], "newton": st["newton_its"], "krylov": st["krylov_its"],
+                   "fnorm_inf": st["fnorm_inf"], "seconds": secs, "zeta_max": float(nv["zeta"].max()),
+                   "zeta_min": float(nv["zeta"].min())}
+            rec.update(wave_heights(mesh.x(), mesh.y(), nv["zeta"], nv["zeta_x"], nv["zeta_y"]))
+            pair[kind] = rec
+            fields[kind] = nv["zeta"]
+            log(json.dumps({"eps": e, kind: rec}))
+            if on_case:
+                on_case(rep, e, kind, nv)
+        if pair["bump"]["status"] == 0 and pair["pressure"]["status"] == 0:
+            pz = p.reshape(mesh.M, mesh.N)
+            d = fields["bump"] - (fields["pressure"] + F * F * pz)
+            pair["linear_relation_defect"] = float(np.abs(d).max() / np.abs(fields["bump"]).max())
+        rep["pairs"].append(pair)
+        if on_case:
+            on_case(rep, e, None, None)
+    ctx.set_surface_pressure(None)
+    ctx.close()
+    return rep
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="super", choices=["super", "sub"])
+    ap.add_argument("--case", default="super", choices=["super", "sub", "compare"],
+                    help="compare: bump vs equivalent pressure at eps = the first --eps (Sec. 6)")
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1, 0.5, 1.0, 1.5, 2.0, 2.5, 2.75])
     ap.add_argument("--F", type=float, default=None, help="Froude number of the supercritical case (3)")
     ap.add_argument("--half-band", type=int, default=3)
@@ -153,6 +243,20 @@ def main(argv=None):
     import __graft_entry__
     __graft_entry__.build()
     saved = {}
+    if a.case == "compare":
+        def on_case(rep, eps, kind, nv):
+            if a.out:
+                with open(a.out, "w") as fh:
+                    json.dump(rep, fh, indent=1)
+            if a.fields and kind is not None:
+                for k in ("zeta", "zeta_x", "zeta_y"):
+                    saved[f"{kind}_{k}_eps{eps:g}"] = nv[k]
+                np.savez_compressed(a.fields, **saved)
+
+        rep = compare_bump_pressure(a.eps[0], a.half_band, max_newton=a.max_newton,
+                                    log=lambda m: print(m, file=sys.stderr, flush=True), on_case=on_case)
+        print(json.dumps(rep))
+        return 0
 
     def on_stage(rep, eps, nv):
         if a.out:

@@ -178,6 +178,42 @@ def config_subcritical_281(eps: float = 0.1):
     return mesh, gaussian_bumps(mesh, [(eps, 0.5, 0.0, 0.0)]), 0.6
 
 
+def gaussian_equivalent_pressure(mesh: Mesh, eps: float, delta: float, F: float) -> np.ndarray:
+    """The applied surface pressure whose linear wake equals that of the
+    Gaussian bump beta + 1 = eps exp(-(x^2 + y^2) / (2 delta^2)) (Sec. 6, the
+    radial integral for p(x, y); Sec. 4.1: its transform is sech(k) times the
+    bump's over F^2):
+
+        p(r) = eps delta^2 / F^2  int_0^inf k sech(k) exp(-delta^2 k^2 / 2) J0(k r) dk.
+
+    An input of the pressure-forced problem (the ship-wake model), evaluated
+    once on the host: Simpson's rule in k on [0, k_max] (the Gaussian factor
+    is below 1e-19 beyond k_max) at a step resolving J0 at the largest node
+    radius, on a radial grid 1/20 of the mesh spacing, interpolated linearly
+    to the nodes.  Nodal values, flat, index i + N j."""
+    from scipy.special import j0
+
+    X, Y = np.meshgrid(mesh.x(), mesh.y(), indexing="xy")
+    r_node = np.hypot(X, Y).ravel()
+    r_max = float(r_node.max())
+    dr = min(mesh.dx, mesh.dy) / 20.0
+    r = np.arange(0.0, r_max + 2.0 * dr, dr)
+    k_max = math.sqrt(2.0 * 45.0) / delta
+    n_k = int(math.ceil(k_max * max(r_max, 1.0) / 0.05))
+    n_k += n_k % 2  # Simpson needs an even number of intervals
+    k = np.linspace(0.0, k_max, n_k + 1)
+    wk = np.full(n_k + 1, 2.0)
+    wk[1::2] = 4.0
+    wk[0] = wk[-1] = 1.0
+    wk *= (k[1] - k[0]) / 3.0
+    g = wk * k / np.cosh(k) * np.exp(-0.5 * (delta * k) ** 2)
+    p_r = np.empty(r.size)
+    for a in range(0, r.size, 512):
+        p_r[a:a + 512] = j0(np.outer(r[a:a + 512], k)) @ g
+    p_r *= eps * delta * delta / (F * F)
+    return np.interp(r_node, r, p_r)
+
+
 def mesh_box(N: int, M: int, dx: float, dy: float, half: int = 0, x1: float | None = None) -> Mesh:
     """A mesh of N x M nodes with the upstream edge at about 28% of the
     x-extent upstream of the origin, symmetric in y."""

@@ -52,3 +52,21 @@ def test_needs_columns_in_range():
     x, y, z, zx, zy, _ = _v_ridge(20.0, 0.1, 1.0)
     with pytest.raises(ValueError):
         wake_metrics(x, y, z, zx, zy, x_from=100.0, x_to=200.0)
+
+
+def test_wave_heights_of_a_synthetic_subcritical_wake():
+    """Transverse waves A cos(k x) confined near the centreline plus one
+    divergent crest of height D at 19 degrees: the heights come back."""
+    from paper_1709_08803_gb300.paper_scale import wave_heights
+    mesh, _, _ = W.config_subcritical_281(0.1)
+    x, y = mesh.x(), mesh.y()
+    X, Y = np.meshgrid(x, y)
+    A, D, k = 0.03, 0.08, 2.78
+    xc, yc = 10.0, 10.0 * math.tan(math.radians(19.0))
+    z = A * np.cos(k * X) * np.exp(-Y * Y) * (X > 0) \
+        + D * np.exp(-((X - xc) ** 2 + (np.abs(Y) - yc) ** 2) / 0.1)
+    zx, zy = np.gradient(z, x, axis=1), np.gradient(z, y, axis=0)
+    h = wave_heights(x, y, z, zx, zy)
+    assert h["transverse_height"] == pytest.approx(A, rel=2e-3)
+    assert h["divergent_crest"] == pytest.approx(D, rel=2e-2)
+    assert h["downstream_steepness"] >= D * math.sqrt(2.0 / 0.1) * math.exp(-0.5) * 0.9
