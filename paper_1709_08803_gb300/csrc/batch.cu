@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <new>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -180,7 +181,8 @@ int bfs_batch_setup(int B, const bfs_mesh *meshes, const bfs_topo *topos, const 
     if (!out) return berr(nullptr, BFS_EINVAL, "out is NULL");
     *out = nullptr;
     if (B < 1 || B > 4096 || !meshes || !topos || !F) return berr(nullptr, BFS_EINVAL, "bad batch arguments");
-    bfs_batch *b = new bfs_batch();
+    bfs_batch *b = new (std::nothrow) bfs_batch();
+    if (!b) return berr(nullptr, BFS_ENOMEM, "host allocation failed");
     b->B = B;
     bfs_options base;
     if (opt) base = *opt;

@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <new>
 #include <string>
 #include <vector>
 
@@ -432,7 +433,8 @@ int bfs_cno_create(int H, int W, int Bmax, bfs_cno **out)
     if (!out) return ferr(nullptr, BFS_EINVAL, "out is NULL");
     *out = nullptr;
     if (H < 3 || W < 3 || Bmax < 1) return ferr(nullptr, BFS_EINVAL, "bad grid or batch size");
-    bfs_cno *n = new bfs_cno();
+    bfs_cno *n = new (std::nothrow) bfs_cno();
+    if (!n) return ferr(nullptr, BFS_ENOMEM, "host allocation failed");
     n->H = H; n->W = W; n->Bmax = Bmax; n->np = n_params();
     const size_t P = (size_t)Bmax * H * W;
     bool ok = cudaMalloc(&n->p, sizeof(float) * (4 * (size_t)n->np + 4)) == cudaSuccess;
