@@ -34,6 +34,9 @@ UNIT = "pair-evals/s"
 # algorithmic work of the FP32C pair kernel per (target half point, source node)
 # index pair: 46 FP32 ALU instructions + 5 MUFU rsqrt = 51 issue slots
 INSTR_PER_INDEX_PAIR = 51
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP32 sweep launch at
+# 181x61 from an ncu capture of the current kernel; None until captured
+APPLY_TRAFFIC = None
 
 
 def _pc_prec(args):
@@ -240,7 +243,8 @@ def run_apply(args):
     torch.cuda.nvtx.range_pop()
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
-    h = max(1, round(mesh.M / 20))
+    pinfo = ctx.precond_info()
+    h = pinfo["half_band"]
     nb = 3 * (mesh.N + 1)
     blocks = sum(min(k, h) + 1 + min(mesh.M - 1 - k, h) for k in range(mesh.M))
     esz = 4 if args.precond == "fp32" else 8
@@ -250,7 +254,8 @@ def run_apply(args):
     ach = nbytes / (ms / 1e3) / 1e9
     print(json.dumps({"mode": "apply", "metric": "preconditioner sweeps at 181x61", "unit": "ms",
                       "value": ms, "steps": args.steps, "warmup": args.warmup,
-                      "sweep_steps": 2 * mesh.M, "us_per_sweep_step": ms * 1e3 / (2 * mesh.M),
+                      "sweep_steps": pinfo["sweep_steps"], "sweep_chains": pinfo["chains"],
+                      "us_per_sweep_step": ms * 1e3 / pinfo["sweep_steps"],
                       "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                                    "frac": ach / hbm, "algorithmic_bytes": nbytes,
                                    "peak_source": f"hbm_gbs of the {src} peaks file"}}))
@@ -565,7 +570,8 @@ def main():
                 "df64_pair_kernel_avg_ms": msdf / max(ndf, 1) if ndf else None,
                 "share_of_step": (ms32 + ms64 + msdf) / (prof_wall_ms * prof_steps)}
     # the preconditioner apply streams every stored factor block once (HBM-bound)
-    h = int(opts.half_band if opts.half_band > 0 else max(1, round(mesh.M / 20)))
+    pinfo = ctx.precond_info()
+    h = pinfo["half_band"]
     nb = 3 * (mesh.N + 1)
     blocks = sum(min(k, h) + 1 + min(mesh.M - 1 - k, h) for k in range(mesh.M))
     esz = 4 if args.precond == "fp32" else 8
@@ -573,14 +579,14 @@ def main():
     avg_ap = msap / max(nap, 1)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roofline_apply = {"bound": "hbm",
-                      "kernel": ("k_apply_tma (FP32 block-banded LU sweeps, bulk-copy ring)" if esz == 4
-                                 else "k_apply_coop (FP64 block-banded LU sweeps)"),
-                      "sweep_steps": 2 * mesh.M,
-                      "us_per_sweep_step": avg_ap * 1e3 / (2 * mesh.M) if nap else None,
+                      "kernel": ("k_apply_sweep (FP32 block-banded LU sweeps, task table, bulk-copy ring)"
+                                 if esz == 4 else "k_apply_coop (FP64 block-banded LU sweeps)"),
+                      "sweep_steps": pinfo["sweep_steps"], "sweep_chains": pinfo["chains"],
+                      "us_per_sweep_step": avg_ap * 1e3 / pinfo["sweep_steps"] if nap else None,
                       "achieved": apply_bytes / (avg_ap / 1e3) / 1e9 if nap else None, "peak": hbm,
                       "unit": "GB/s", "frac": (apply_bytes / (avg_ap / 1e3) / 1e9) / hbm if nap else None,
                       # dram bytes read + written per launch, from an ncu capture of this kernel at 181x61
-                      "traffic": 501.1e6 if (esz == 4 and args.F == 0.7) else None,
+                      "traffic": APPLY_TRAFFIC if (esz == 4 and args.F == 0.7) else None,
                       "algorithmic_bytes": apply_bytes, "avg_launch_ms": avg_ap,
                       "launches": nap, "peak_source": f"hbm_gbs of the {src} peaks file",
                       "share_of_step": msap / (prof_wall_ms * prof_steps)}

@@ -126,6 +126,11 @@ typedef struct {
                               J s_{k-1}| | / |F_{k-1}|, safeguarded by eta_{k-1}^1.618
                               when that exceeds 0.1, kept in [eta, 0.9]; eta_0 =
                               max(eta, 0.1) */
+    int wait_polls;        /* polls of a device-side wait (the tags of the preconditioner
+                              sweeps, the grid barriers of the cooperative kernels) before
+                              it gives up: the kernel raises the context's timeout bit,
+                              returns, and bfs_check_finite / bfs_solve report
+                              BFS_ETIMEOUT.  <= 0 (default): about one second per wait. */
 } bfs_options;
 
 typedef struct {
@@ -188,8 +193,10 @@ double bfs_pair_evals(const bfs_ctx *ctx);
    entry raises the context's NaN flag (read by bfs_check_finite). */
 int bfs_residual(bfs_ctx *ctx, const double *u, double *Fu, int precision, void *stream);
 
-/* Synchronises stream and returns BFS_ENAN if any residual evaluated since the
-   previous call was non-finite, else BFS_OK; clears the flag. */
+/* Synchronises stream and returns BFS_ETIMEOUT if a device-side wait gave up
+   (see wait_polls; the sweep vectors are then reset, so the next call runs
+   normally), else BFS_ENAN if any residual evaluated since the previous call
+   was non-finite, else BFS_OK; clears the flags. */
 int bfs_check_finite(bfs_ctx *ctx, void *stream);
 
 /* Jz = (F(u + h z) - Fu) / h, the finite-difference Jacobian-vector product
@@ -206,6 +213,13 @@ int bfs_jvp(bfs_ctx *ctx, const double *u, const double *Fu, const double *z, do
    and n only.  half_band < 0 uses the option's value.  Synchronous.
    Errors: BFS_ESINGULAR, BFS_ENOMEM, BFS_ECUDA. */
 int bfs_precond_factor(bfs_ctx *ctx, int half_band, void *stream);
+
+/* Shape of the factored preconditioner: info[0] the half band h, info[1] the
+   first middle slice t of the two-ended order (-1: one-ended), info[2] the
+   chains the FP32 sweeps run side by side (0: FP64 sweeps), info[3] the
+   dependent steps of the longest chain (tasks of the sweep table; 2M for the
+   FP64 sweeps).  BFS_ENOPREC before bfs_precond_factor. */
+int bfs_precond_info(const bfs_ctx *ctx, int *info4);
 
 /* z = P^{-1} r with the factored preconditioner.  r, z: device, length n,
    in the order of u (r may equal z).  BFS_ENOPREC before bfs_precond_factor. */
@@ -245,6 +259,36 @@ int bfs_unpack(bfs_ctx *ctx, const double *u, double *out, void *stream);
    the whole mirrored domain and a zero y component).  Synchronous when
    force_host is given. */
 int bfs_bottom_pressure(bfs_ctx *ctx, const double *u, double *p, double *force_host, void *stream);
+
+/* The task table of the FP32 preconditioner sweeps for M slices and half band
+   half_band (App. A), without a GPU: the one-ended block LU (twisted = 0: the
+   forward chain, then the backward chain) or the two-ended one (twisted = 1:
+   a chain from each end, the middle system, the chains back outwards; the
+   order bfs_precond_factor takes when the FP32 sweeps can run it).  Writes
+   the tasks as 16 ints each into tasks_out (room for cap tasks; NULL to only
+   count them): {k, out, nblk, 0, m[4], vec[4], uid[4]} -- task uid u writes
+   slice k of y (out 0, adding the right-hand side) or z (out 1) as
+   sum_p sign_p B(k, m[p]) v_p, v_p being z_{m[p]} if vec bit 0 is set (else
+   y_{m[p]}), sign + if vec bit 1 is set, and written by task uid[p]; vec bits
+   2-3 say where the kernel's threads find v_p (0: loaded at the end of the
+   step before; 1: held in registers since it was the critical vector of an
+   earlier task, bits 4-5 its index, newest first; 2: the critical vector,
+   written by the group's previous task and polled last).  Group 0's
+   tasks come first; ntask_out (optional, 2 ints) receives the tasks per group.
+   Returns the number of tasks, or BFS_EINVAL (half_band > 3, M < 1, or
+   cap too small). */
+int bfs_sweep_schedule(int M, int half_band, int twisted, int *tasks_out, int cap, int *ntask_out);
+
+/* Test hook for the timeout path of the sweeps' waits: the next FP32 sweep
+   launch of ctx (bfs_precond_apply or an Arnoldi step launched directly, not
+   replayed from a graph) waits, in task `task` of the table above, for a
+   vector slice no task of that launch writes, so that its waits run out after
+   wait_polls polls and it returns with the timeout bit raised.  The table is
+   restored right after that launch; bfs_check_finite then returns
+   BFS_ETIMEOUT and resets the sweep vectors, and the next apply is normal.
+   BFS_EINVAL unless the preconditioner is factored with FP32 task-table
+   sweeps and the task multiplies at least one block. */
+int bfs_debug_stall_sweep(bfs_ctx *ctx, int task);
 
 /* Profiling.  bfs_profile_enable(ctx, 1) records a CUDA event pair on the
    launching stream around every pair-kernel launch and every preconditioner

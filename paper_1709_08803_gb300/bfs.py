@@ -52,7 +52,8 @@ class bfs_options(ctypes.Structure):
                 ("time_budget_s", ctypes.c_double), ("src_splits", ctypes.c_int),
                 ("outer_precision", ctypes.c_int), ("precond_precision", ctypes.c_int),
                 ("refine_below", ctypes.c_double), ("stall_newton", ctypes.c_int),
-                ("surface_tension", ctypes.c_double), ("forcing", ctypes.c_int)]
+                ("surface_tension", ctypes.c_double), ("forcing", ctypes.c_int),
+                ("wait_polls", ctypes.c_int)]
 
 
 class bfs_stats(ctypes.Structure):
@@ -125,6 +126,10 @@ def lib():
         L.bfs_profile_enable.argtypes = [_VP, ctypes.c_int]
         L.bfs_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_ulonglong)]
+        L.bfs_sweep_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, C(ctypes.c_int),
+                                         ctypes.c_int, C(ctypes.c_int)]
+        L.bfs_debug_stall_sweep.argtypes = [_VP, ctypes.c_int]
+        L.bfs_precond_info.argtypes = [_VP, C(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -242,6 +247,18 @@ class Context:
         self._check(lib().bfs_precond_apply(self._ctx, self._vec(r), self._vec(out), _stream(stream)))
         return out
 
+    def precond_info(self) -> dict:
+        """Half band, two-ended split (-1: one-ended), sweep chains and the
+        dependent steps of the longest chain of the factored preconditioner."""
+        info = (ctypes.c_int * 4)()
+        self._check(lib().bfs_precond_info(self._ctx, info))
+        return {"half_band": info[0], "twist": info[1], "chains": info[2], "sweep_steps": info[3]}
+
+    def debug_stall_sweep(self, task: int):
+        """Test hook: the next FP32 sweep launch waits in `task` for a vector no
+        task writes (its waits run out after the option wait_polls)."""
+        self._check(lib().bfs_debug_stall_sweep(self._ctx, int(task)))
+
     def solve(self, u, stream=None, raise_on_error: bool = True):
         st = bfs_stats()
         rc = lib().bfs_solve(self._ctx, self._vec(u), ctypes.byref(st), _stream(stream))
@@ -339,6 +356,22 @@ def residual_static(mesh, beta, beta_x, beta_y, F: float, u, out=None, precision
     if rc != BFS_OK:
         raise BfsError(rc, lib().bfs_static_last_error().decode())
     return out
+
+
+def sweep_schedule(M: int, half_band: int, twisted: bool):
+    """Task table of the FP32 preconditioner sweeps (host only, no GPU): an
+    (ntasks, 16) int array of {k, out, nblk, 0, m[4], vec[4], uid[4]} rows and
+    the number of tasks of each CTA group."""
+    L = lib()
+    cnt = (ctypes.c_int * 2)()
+    n = L.bfs_sweep_schedule(int(M), int(half_band), int(bool(twisted)), None, 0, cnt)
+    if n < 0:
+        raise BfsError(n, "invalid sweep schedule arguments")
+    buf = (ctypes.c_int * (16 * max(n, 1)))()
+    n2 = L.bfs_sweep_schedule(int(M), int(half_band), int(bool(twisted)), buf, n, cnt)
+    if n2 != n:
+        raise BfsError(n2, "sweep schedule changed between calls")
+    return np.frombuffer(buf, dtype=np.int32, count=16 * n).reshape(n, 16).copy(), (cnt[0], cnt[1])
 
 
 class Batch:

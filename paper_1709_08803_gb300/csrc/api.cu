@@ -148,6 +148,8 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     c->x1 = mesh->x1; c->y1 = mesh->y1; c->dx = mesh->dx; c->dy = mesh->dy; c->F = F;
     c->beta_max = beta_max;
     c->opt = o;
+    c->pc_twist = -1;
+    c->dbg_stall_task = -1;
     c->n = 3 * (N + 1) * M;
     c->Nt = (N - 1) * M;
     c->NM = (int)NM;
@@ -288,7 +290,12 @@ int bfs_check_finite(bfs_ctx *c, void *stream)
     BFS_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-    if (flag & 2) return set_err(c, BFS_ETIMEOUT, "a wait in the preconditioner sweeps timed out");
+    if (flag & 2) {
+        // entries a timed-out sweep left behind must not match a later launch's tags
+        int rc = bfs::flow_reset(c, s);
+        if (rc) return rc;
+        return set_err(c, BFS_ETIMEOUT, "a device-side wait timed out");
+    }
     if (flag) return set_err(c, BFS_ENAN, "a residual entry was not finite");
     return BFS_OK;
 }
@@ -306,6 +313,17 @@ int bfs_precond_factor(bfs_ctx *c, int half_band, void *stream)
 {
     if (!c) return BFS_EINVAL;
     return bfs::precond_factor(c, half_band, (cudaStream_t)stream);
+}
+
+int bfs_precond_info(const bfs_ctx *c, int *info)
+{
+    if (!c || !info) return BFS_EINVAL;
+    if (!c->pc_ready) return BFS_ENOPREC;
+    info[0] = c->pc_h;
+    info[1] = c->pc_twist;
+    info[2] = c->sweep_table ? c->sweep_groups : (c->d_pc32 ? 1 : 0);
+    info[3] = c->sweep_table ? std::max(c->sweep_ntask[0], c->sweep_ntask[1]) : 2 * c->M;
+    return BFS_OK;
 }
 
 int bfs_precond_apply(bfs_ctx *c, const double *r, double *z, void *stream)

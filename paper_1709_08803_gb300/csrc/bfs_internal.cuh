@@ -49,6 +49,28 @@ struct BatchVariant {
     int tpb, tpt;
 };
 
+// One step of the FP32 preconditioner sweeps (apply.cu): the slice k whose
+// rows it finishes and the stored blocks (k, m[p]) it multiplies.
+//   out 0: y_k = r_k - sum_p B(k, m_p) v_p;  out 1: z_k = sum_p +-B(k, m_p) v_p
+//   vec[p] bit 0: v_p is z_{m_p} (else y_{m_p}); bit 1: sign + (else -);
+//          bits 2-3: where a thread finds its columns of v_p (SW_EARLY, SW_WIN,
+//          SW_CRIT); bits 4-5: the register-window index (SW_WIN)
+//   uid[p]: the task that wrote v_p (tasks are numbered group 0 first)
+constexpr int SW_BMAX = 4;
+constexpr int SW_HW = 2;  // register window: the last SW_HW critical vectors
+enum { SW_EARLY = 0, SW_WIN = 1, SW_CRIT = 2 };
+struct SweepTask {
+    int k, out, nblk, pad;
+    int m[SW_BMAX], vec[SW_BMAX], uid[SW_BMAX];
+};
+
+struct SweepPlan {
+    int twist = -1;          // first middle slice of the two-ended order, or -1
+    int groups = 1;          // chains run side by side (CTA groups)
+    int ntask[2] = {0, 0};   // tasks per group
+    std::vector<SweepTask> tasks;
+};
+
 struct PairPlan {
     int tpb;        // threads per CTA
     int tpt;        // targets per thread
@@ -109,6 +131,13 @@ struct bfs_ctx {
     unsigned long long *d_flow;  // tagged y and z of the FP32 sweeps, 2 M nb, then the tag word
     unsigned long long flow_count;  // FP32 sweep launches since the tags were reset
     int capturing;               // a CUDA graph is being captured on the solver stream
+    int pc_twist;                // two-ended factor order: first middle slice; -1: one-ended
+    bfs::SweepTask *d_tasks;     // task table of the FP32 sweeps
+    std::vector<bfs::SweepTask> h_tasks;
+    int sweep_table;             // 1: the task-table kernel runs the FP32 sweeps
+    int sweep_groups, sweep_ntask[2], sweep_ntags, sweep_rpc, sweep_nslot;
+    size_t sweep_dyn;
+    int dbg_stall_task;          // test hook: task whose first wait is made unsatisfiable, or -1
 
     // Arnoldi steps of bfs_solve replayed as CUDA graphs, one per (Krylov
     // index j, base residual buffer); cleared whenever a captured argument
@@ -149,6 +178,9 @@ int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s);
 int precond_make_f32(bfs_ctx *c, cudaStream_t s);
 int apply_flow_launch(bfs_ctx *c, const double *r, double *z, cudaStream_t s);
 int flow_wrap_check(bfs_ctx *c, cudaStream_t s);
+int flow_reset(bfs_ctx *c, cudaStream_t s);
+int sweep_plan(int M, int h, int twisted, SweepPlan &P);
+int sweep_twist_ok(bfs_ctx *c, int h);
 extern const BatchVariant kBatchVariants[];
 extern const int kNumBatchVariants;
 int batch_pairs_occupancy(int v, int *blocks_per_sm);

@@ -18,13 +18,22 @@
 //   means of the two neighbouring nodes, H(k, n) = (T(k,n) + T(k+1,n)) / 2.
 //
 // Factorisation (no pivoting across blocks; partial pivoting inside the
-// diagonal blocks by Gauss-Jordan inversion):
+// diagonal blocks by Gauss-Jordan inversion), one-ended:
 //   for k: D_k^-1;  W_kj = D_k^-1 U_kj;  S_ij -= S_ik W_kj;  L_ik = S_ik D_k^-1
 // stored in place: diagonal slot D_k^-1, lower slots L, upper slots W, so that
 //   forward  y_k = x_k - sum_i L_ki y_i
 //   backward z_k = D_k^-1 y_k - sum_j W_kj z_j.
+// Two-ended ("twisted", for the FP32 sweeps of apply.cu): the same step for
+// slices k = 0..t-1 with the coupled slices above them, and for k = M-1 down to
+// t+h with the coupled slices below them (W'_kj = D_k^-1 S_kj in the lower
+// slots of row k, U'_ik = S_ik D_k^-1 in the upper slots of column k).  The two
+// chains meet only in the h middle slices t..t+h-1, whose Schur complement C
+// (h nb square, both chains' updates added) is inverted whole; C^-1 replaces
+// the middle-middle blocks.  Both orders are exact block LU of the same banded
+// matrix; the second halves the sweeps' chain of dependent steps.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "bfs_internal.cuh"
@@ -219,42 +228,30 @@ __global__ void k_form_tension(PcArgs a, double *pc)
 }
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan inversion with partial pivoting of one nb x nb block, one launch
-// per pivot column on ping-pong buffers X = [D | I] (nb x 2nb, row-major).
+// Gauss-Jordan inversion with partial pivoting on ping-pong buffers
+// X = [D | I] (n x 2n, row-major), one or two matrices in one cooperative
+// launch: CTA b works on matrix b % nmat, a bounded grid barrier between pivot
+// columns (see grid_sync below).
 // ---------------------------------------------------------------------------
-__global__ void k_gj_load(const double *__restrict__ D, double *__restrict__ X, int nb)
-{
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * 2 * nb;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int r = (int)(e / (2 * nb)), c = (int)(e % (2 * nb));
-        X[e] = c < nb ? D[(size_t)r * nb + c] : (c - nb == r ? 1.0 : 0.0);
-    }
-}
-
-__global__ void k_gj_store(const double *__restrict__ X, double *__restrict__ D, int nb)
-{
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int r = (int)(e / nb), c = (int)(e % nb);
-        D[e] = X[(size_t)r * 2 * nb + nb + c];
-    }
-}
-
-// Cooperative form of the same inversion: one launch per diagonal block, a
-// bounded grid barrier between pivot columns (see grid_sync below).
 struct CoopBar;
-__device__ bool grid_sync(CoopBar *b, int *flag);
+__device__ bool grid_sync(CoopBar *b, int *flag, unsigned int spin);
 
-__global__ void __launch_bounds__(256) k_gj_coop(double *X0, double *X1, int nb, int *pivflag,
-                                                 CoopBar *bar, int *flag)
+struct GjSet {
+    double *X0[2], *X1[2];  // ping-pong buffers [D | I] of each matrix (n x 2n)
+    int nmat;
+};
+
+__global__ void __launch_bounds__(256) k_gj_coop(GjSet set, int nb, int *pivflag, CoopBar *bar, int *flag,
+                                                 unsigned int spin)
 {
     __shared__ double bv[8];
     __shared__ int bi[8];
     __shared__ int piv;
     __shared__ double pval;
     const int ld = 2 * nb;
-    const double *Xi = X0;
-    double *Xo = X1;
+    const int mat = blockIdx.x % set.nmat, lb = blockIdx.x / set.nmat, lg = gridDim.x / set.nmat;
+    const double *Xi = set.X0[mat];
+    double *Xo = set.X1[mat];
     for (int c = 0; c < nb; c++) {
         double best = -1.0;
         int bidx = c;
@@ -276,12 +273,12 @@ __global__ void __launch_bounds__(256) k_gj_coop(double *X0, double *X1, int nb,
                 if (bv[w] > b || (bv[w] == b && bi[w] < i)) { b = bv[w]; i = bi[w]; }
             piv = i;
             pval = __ldcg(Xi + (size_t)i * ld + c);
-            if (!(b > 0.0) && blockIdx.x == 0) atomicOr(pivflag, 1);
+            if (!(b > 0.0) && lb == 0) atomicOr(pivflag, 1);
         }
         __syncthreads();
         const int p = piv;
         const double ip = pval != 0.0 ? 1.0 / pval : 0.0;
-        for (int r = blockIdx.x; r < nb; r += gridDim.x) {
+        for (int r = lb; r < nb; r += lg) {
             const int src = (r == c) ? p : ((r == p) ? c : r);
             const double *xs = Xi + (size_t)src * ld;
             const double *xp = Xi + (size_t)p * ld;
@@ -294,10 +291,39 @@ __global__ void __launch_bounds__(256) k_gj_coop(double *X0, double *X1, int nb,
                     __stcg(xo + q, fma(-f, __ldcg(xp + q), __ldcg(xs + q)));
             }
         }
-        if (!grid_sync(bar, flag)) return;
+        if (!grid_sync(bar, flag, spin)) return;
         const double *t = Xi;
         Xi = Xo;
         Xo = const_cast<double *>(t);
+    }
+}
+
+// One nb x nb block into (or out of) the n x 2n Gauss-Jordan buffer at block
+// position (a, b); the identity in the right half.
+__global__ void k_gj_put(const double *__restrict__ D, double *__restrict__ X, int nb, int n, int a, int b)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / nb), c = (int)(e % nb);
+        X[(size_t)(a * nb + r) * 2 * n + b * nb + c] = D[e];
+    }
+}
+
+__global__ void k_gj_eye(double *__restrict__ X, int n)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        X[(size_t)r * 2 * n + n + c] = r == c ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_gj_get(const double *__restrict__ X, double *__restrict__ D, int nb, int n, int a, int b)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / nb), c = (int)(e % nb);
+        D[e] = X[(size_t)(a * nb + r) * 2 * n + n + b * nb + c];
     }
 }
 
@@ -391,7 +417,7 @@ struct CoopBar {
 };
 
 // Barrier of the Gauss-Jordan kernel (one per pivot column).
-__device__ bool grid_sync(CoopBar *b, int *flag)
+__device__ bool grid_sync(CoopBar *b, int *flag, unsigned int spin)
 {
     __shared__ int ok;
     __syncthreads();
@@ -408,7 +434,7 @@ __device__ bool grid_sync(CoopBar *b, int *flag)
         } else {
             unsigned int spins = 0;
             while (*vgen == g) {
-                if (++spins > (1u << 24)) {
+                if (++spins > spin) {
                     atomicOr(flag, 2);
                     ok = 0;
                     break;
@@ -427,7 +453,8 @@ __device__ bool grid_sync(CoopBar *b, int *flag)
 // reaches e * gridDim.x.  Arrival is a release add, the wait an acquire load,
 // so no separate fences are needed.  The wait is bounded (about a second);
 // on timeout bit 2 of the flag is raised and false is returned.
-__device__ __forceinline__ bool grid_sync_epoch(unsigned int *count, unsigned int epoch, int *flag)
+__device__ __forceinline__ bool grid_sync_epoch(unsigned int *count, unsigned int epoch, int *flag,
+                                                unsigned int spin)
 {
     __shared__ int ok;
     __syncthreads();
@@ -440,7 +467,7 @@ __device__ __forceinline__ bool grid_sync_epoch(unsigned int *count, unsigned in
         while (v < target) {
             asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
             if (v >= target) break;
-            if (++spins > (1u << 24)) {
+            if (++spins > spin) {
                 atomicOr(flag, 2);
                 ok = 0;
                 break;
@@ -459,6 +486,7 @@ struct ApplyArgs {
     int nb, NB, M, h;
     CoopBar *bar;
     int *flag;
+    unsigned int spin;
 };
 
 constexpr int AP_TPB = 1024;
@@ -509,7 +537,7 @@ __global__ void __launch_bounds__(AP_TPB, 1) k_apply_coop(ApplyArgs a)
         int g = e / (NB * M), rem = e % (NB * M), l = rem / NB, p = rem % NB;
         __stcg(a.x + (size_t)l * nb + g * NB + p, a.r[e]);
     }
-    if (!grid_sync_epoch(cnt, ++epoch, a.flag)) return;
+    if (!grid_sync_epoch(cnt, ++epoch, a.flag, a.spin)) return;
     for (int pass = 0; pass < 2; pass++) {
         for (int kk = 0; kk < M; kk++) {
             const int k = pass == 0 ? kk : M - 1 - kk;
@@ -564,7 +592,7 @@ __global__ void __launch_bounds__(AP_TPB, 1) k_apply_coop(ApplyArgs a)
                 }
                 __syncthreads();
             }
-            if (!grid_sync_epoch(cnt, ++epoch, a.flag)) return;
+            if (!grid_sync_epoch(cnt, ++epoch, a.flag, a.spin)) return;
         }
     }
     for (int e = gtid; e < n; e += gstride) {
@@ -591,8 +619,14 @@ void precond_free(bfs_ctx *c)
     cudaFree(c->d_pc);
     cudaFree(c->d_pc32);
     cudaFree(c->d_flow);
+    cudaFree(c->d_tasks);
     c->d_pc32 = nullptr;
     c->d_flow = nullptr;
+    c->d_tasks = nullptr;
+    c->h_tasks.clear();
+    c->sweep_table = 0;
+    c->sweep_ntags = 0;
+    c->pc_twist = -1;
     cudaFree(c->d_gj);
     cudaFree(c->d_rowsum5);
     cudaFree(c->d_pivflag);
@@ -600,6 +634,35 @@ void precond_free(bfs_ctx *c)
     c->d_pc = c->d_gj = c->d_rowsum5 = c->d_perm_a = c->d_perm_b = nullptr;
     c->d_pivflag = nullptr;
     c->pc_ready = 0;
+}
+
+static unsigned int wait_spin(const bfs_ctx *c)
+{
+    return c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 24);
+}
+
+// Gauss-Jordan inversion of one or two n x n matrices already loaded as
+// [D | I] into set.X0; returns in *res the buffers holding [. | D^-1].
+static int gj_invert(bfs_ctx *c, GjSet set, int n, double **res, cudaStream_t s)
+{
+    int gj_per_sm = 0;
+    BFS_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gj_per_sm, k_gj_coop, 256, 0));
+    if (gj_per_sm < 1) {
+        c->err = "Gauss-Jordan kernel cannot be resident";
+        return BFS_ECUDA;
+    }
+    int grid = std::min(num_sms(c->device) * std::min(gj_per_sm, 2), n * set.nmat);
+    grid -= grid % set.nmat;
+    CoopBar *bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
+    BFS_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+    int nv = n;
+    int *pf = c->d_pivflag, *fl = c->d_flag;
+    unsigned int spin = wait_spin(c);
+    void *args[] = {&set, &nv, &pf, &bar, &fl, &spin};
+    BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(grid), dim3(256), args, 0, s));
+    c->launches++;
+    for (int i = 0; i < set.nmat; i++) res[i] = (n % 2 == 0) ? set.X0[i] : set.X1[i];  // after n ping-pong steps
+    return BFS_OK;
 }
 
 int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
@@ -612,13 +675,20 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     const int nb = 3 * (c->N + 1), M = c->M, nd = 2 * h + 1;
     c->nb = nb;
     c->pc_h = h;
+    // the two-ended order whenever the FP32 task-table sweeps can run its two chains
+    int rc = sweep_twist_ok(c, h);
+    if (rc < 0) return rc;
+    const int twist = rc == 1 ? (M - h) / 2 : -1;
     const size_t bsz = (size_t)nb * nb;
     if (cudaMalloc(&c->d_pc, sizeof(double) * bsz * M * nd) != cudaSuccess) {
         cudaGetLastError();
         c->err = "preconditioner storage: out of device memory";
         return BFS_ENOMEM;
     }
-    BFS_CUDA_TRY(c, cudaMalloc(&c->d_gj, sizeof(double) * (bsz * 4 + bsz * (size_t)(h > 0 ? h : 1))));
+    // Gauss-Jordan buffers: two matrices of nb x 2nb ping-pong, or the h nb x 2 h nb
+    // middle system; then h blocks of GEMM scratch
+    const size_t gj_doubles = std::max<size_t>(8 * bsz, twist >= 0 ? 4 * (size_t)h * h * bsz : 0);
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_gj, sizeof(double) * (gj_doubles + bsz * (size_t)(h > 0 ? h : 1))));
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_rowsum5, sizeof(double) * (size_t)c->Nt));
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int) * 8));  // [0] pivot flag, [4..5] grid barrier
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_perm_a, sizeof(double) * 2 * (size_t)c->n));
@@ -641,57 +711,94 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     BFS_CUDA_TRY(c, cudaGetLastError());
 
     auto B = [&](int l, int m) { return c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz; };
-    double *X0 = c->d_gj, *X1 = c->d_gj + 2 * bsz, *tmp = c->d_gj + 4 * bsz;
-    int gj_per_sm = 0;
-    BFS_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gj_per_sm, k_gj_coop, 256, 0));
-    if (gj_per_sm < 1) {
-        c->err = "Gauss-Jordan kernel cannot be resident";
-        return BFS_ECUDA;
-    }
-    const int gj_grid = std::min(num_sms(c->device) * std::min(gj_per_sm, 2), nb);
-    for (int k = 0; k < M; k++) {
-        // D_k^-1 in place
-        k_gj_load<<<512, 256, 0, s>>>(B(k, k), X0, nb);
-        c->launches++;
-        {
-            CoopBar *bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
-            BFS_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
-            double *x0 = X0, *x1 = X1;
-            int nbv = nb;
-            int *pf = c->d_pivflag, *fl = c->d_flag;
-            void *args[] = {&x0, &x1, &nbv, &pf, &bar, &fl};
-            BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(gj_grid), dim3(256),
-                                                        args, 0, s));
+    double *tmp = c->d_gj + gj_doubles;
+    // D_k^-1 in place for the one or two diagonal blocks listed
+    auto invert_diag = [&](const int *ks, int cnt) -> int {
+        GjSet set;
+        set.nmat = cnt;
+        for (int i = 0; i < cnt; i++) {
+            set.X0[i] = c->d_gj + (size_t)i * 4 * bsz;
+            set.X1[i] = set.X0[i] + 2 * bsz;
+            k_gj_put<<<512, 256, 0, s>>>(B(ks[i], ks[i]), set.X0[i], nb, nb, 0, 0);
+            k_gj_eye<<<512, 256, 0, s>>>(set.X0[i], nb);
+            c->launches += 2;
+        }
+        double *res[2];
+        int r = gj_invert(c, set, nb, res, s);
+        if (r) return r;
+        for (int i = 0; i < cnt; i++) {
+            k_gj_get<<<512, 256, 0, s>>>(res[i], B(ks[i], ks[i]), nb, nb, 0, 0);
             c->launches++;
         }
-        double *xi = (nb % 2 == 0) ? X0 : X1;  // after nb ping-pong steps
-        k_gj_store<<<512, 256, 0, s>>>(xi, B(k, k), nb);
-        c->launches++;
-        const int hi = std::min(M - 1, k + h);
-        if (hi > k) {
-            std::vector<const double *> A, Bm;
-            std::vector<double *> C;
-            // W_kj = D_k^-1 U_kj into tmp, then back into the U slots
-            for (int j = k + 1; j <= hi; j++) { A.push_back(B(k, k)); Bm.push_back(B(k, j)); C.push_back(tmp + (j - k - 1) * bsz); }
-            int rc = gemm_batch(c, A, Bm, C, 1.0, 0.0, s);
-            if (rc) return rc;
-            for (int j = k + 1; j <= hi; j++)
-                BFS_CUDA_TRY(c, cudaMemcpyAsync(B(k, j), tmp + (j - k - 1) * bsz, sizeof(double) * bsz,
-                                                cudaMemcpyDeviceToDevice, s));
-            // S_ij -= S_ik W_kj
-            A.clear(); Bm.clear(); C.clear();
-            for (int i = k + 1; i <= hi; i++)
-                for (int j = k + 1; j <= hi; j++) { A.push_back(B(i, k)); Bm.push_back(B(k, j)); C.push_back(B(i, j)); }
-            if ((rc = gemm_batch(c, A, Bm, C, -1.0, 1.0, s))) return rc;
-            // L_ik = S_ik D_k^-1
-            A.clear(); Bm.clear(); C.clear();
-            for (int i = k + 1; i <= hi; i++) { A.push_back(B(i, k)); Bm.push_back(B(k, k)); C.push_back(tmp + (i - k - 1) * bsz); }
-            if ((rc = gemm_batch(c, A, Bm, C, 1.0, 0.0, s))) return rc;
-            for (int i = k + 1; i <= hi; i++)
-                BFS_CUDA_TRY(c, cudaMemcpyAsync(B(i, k), tmp + (i - k - 1) * bsz, sizeof(double) * bsz,
-                                                cudaMemcpyDeviceToDevice, s));
+        BFS_CUDA_TRY(c, cudaGetLastError());
+        return BFS_OK;
+    };
+    // eliminate slice k (D_k^-1 in place) from the coupled slices lo..hi
+    auto eliminate = [&](int k, int lo, int hi) -> int {
+        if (hi < lo) return BFS_OK;
+        std::vector<const double *> A, Bm;
+        std::vector<double *> C;
+        // W_kj = D_k^-1 S_kj into tmp, then back into slot (k, j)
+        for (int j = lo; j <= hi; j++) { A.push_back(B(k, k)); Bm.push_back(B(k, j)); C.push_back(tmp + (j - lo) * bsz); }
+        int r = gemm_batch(c, A, Bm, C, 1.0, 0.0, s);
+        if (r) return r;
+        for (int j = lo; j <= hi; j++)
+            BFS_CUDA_TRY(c, cudaMemcpyAsync(B(k, j), tmp + (j - lo) * bsz, sizeof(double) * bsz,
+                                            cudaMemcpyDeviceToDevice, s));
+        // S_ij -= S_ik W_kj
+        A.clear(); Bm.clear(); C.clear();
+        for (int i = lo; i <= hi; i++)
+            for (int j = lo; j <= hi; j++) { A.push_back(B(i, k)); Bm.push_back(B(k, j)); C.push_back(B(i, j)); }
+        if ((r = gemm_batch(c, A, Bm, C, -1.0, 1.0, s))) return r;
+        // S_ik D_k^-1 into slot (i, k)
+        A.clear(); Bm.clear(); C.clear();
+        for (int i = lo; i <= hi; i++) { A.push_back(B(i, k)); Bm.push_back(B(k, k)); C.push_back(tmp + (i - lo) * bsz); }
+        if ((r = gemm_batch(c, A, Bm, C, 1.0, 0.0, s))) return r;
+        for (int i = lo; i <= hi; i++)
+            BFS_CUDA_TRY(c, cudaMemcpyAsync(B(i, k), tmp + (i - lo) * bsz, sizeof(double) * bsz,
+                                            cudaMemcpyDeviceToDevice, s));
+        return BFS_OK;
+    };
+    if (twist < 0) {
+        for (int k = 0; k < M; k++) {
+            if ((rc = invert_diag(&k, 1))) return rc;
+            if ((rc = eliminate(k, k + 1, std::min(M - 1, k + h)))) return rc;
         }
+    } else {
+        const int t0 = twist, t1 = twist + h;
+        for (int i = 0; i < std::max(t0, M - t1); i++) {
+            int ks[2], cnt = 0;
+            const int kt = i < t0 ? i : -1, kb = M - 1 - i >= t1 ? M - 1 - i : -1;
+            if (kt >= 0) ks[cnt++] = kt;
+            if (kb >= 0) ks[cnt++] = kb;
+            if ((rc = invert_diag(ks, cnt))) return rc;
+            // sequential: both chains may update the same middle-middle blocks
+            if (kt >= 0 && (rc = eliminate(kt, kt + 1, std::min(M - 1, kt + h)))) return rc;
+            if (kb >= 0 && (rc = eliminate(kb, std::max(0, kb - h), kb - 1))) return rc;
+        }
+        // the middle system C (slices t0..t1-1, h nb square) inverted whole
+        const int hn = h * nb;
+        GjSet set;
+        set.nmat = 1;
+        set.X0[0] = c->d_gj;
+        set.X1[0] = c->d_gj + 2 * (size_t)hn * hn;
+        for (int ia = 0; ia < h; ia++)
+            for (int ib = 0; ib < h; ib++) {
+                k_gj_put<<<512, 256, 0, s>>>(B(t0 + ia, t0 + ib), set.X0[0], nb, hn, ia, ib);
+                c->launches++;
+            }
+        k_gj_eye<<<1024, 256, 0, s>>>(set.X0[0], hn);
+        c->launches++;
+        double *res[2];
+        if ((rc = gj_invert(c, set, hn, res, s))) return rc;
+        for (int ia = 0; ia < h; ia++)
+            for (int ib = 0; ib < h; ib++) {
+                k_gj_get<<<512, 256, 0, s>>>(res[0], B(t0 + ia, t0 + ib), nb, hn, ia, ib);
+                c->launches++;
+            }
+        BFS_CUDA_TRY(c, cudaGetLastError());
     }
+    c->pc_twist = twist;
     int flag = 0;
     BFS_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_pivflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -703,7 +810,7 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     // diagonal blocks so ill-conditioned (inverse entries of 1e5-1e7 on small
     // meshes) that FP32 copies of the factors no longer precondition
     if (c->opt.precond_precision == BFS_FP32C && c->opt.surface_tension == 0.0) {
-        int rc = precond_make_f32(c, s);
+        rc = precond_make_f32(c, s);
         if (rc) return rc;
         BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
     }
@@ -731,6 +838,10 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
         if (ev1) cudaEventRecord(ev1, s);
         return BFS_OK;
     }
+    if (c->pc_twist >= 0) {
+        c->err = "two-ended factors need the FP32 sweep kernel";
+        return BFS_ECUDA;
+    }
     if (c->apply_grid <= 0) {
         int per_sm = 0;
         BFS_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_coop, AP_TPB, 0));
@@ -745,6 +856,7 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
     a.nb = c->nb; a.NB = c->N + 1; a.M = c->M; a.h = c->pc_h;
     a.bar = reinterpret_cast<CoopBar *>(c->d_pivflag + 4);
     a.flag = c->d_flag;
+    a.spin = wait_spin(c);
     BFS_CUDA_TRY(c, cudaMemsetAsync(a.bar, 0, sizeof(CoopBar), s));
     void *args[] = {&a};
     BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_apply_coop, dim3(c->apply_grid),

@@ -277,7 +277,7 @@ struct TailBar {
     unsigned int count, gen;
 };
 
-__device__ bool tail_sync(TailBar *b, int *flag)
+__device__ bool tail_sync(TailBar *b, int *flag, unsigned int spin)
 {
     __shared__ int ok;
     __syncthreads();
@@ -294,7 +294,7 @@ __device__ bool tail_sync(TailBar *b, int *flag)
         } else {
             unsigned int spins = 0;
             while (*vgen == g) {
-                if (++spins > (1u << 24)) {
+                if (++spins > spin) {
                     atomicOr(flag, 2);
                     ok = 0;
                     break;
@@ -316,6 +316,7 @@ struct TailArgs {
     int n, cnt, m;
     TailBar *bar;
     int *flag;
+    unsigned int spin;
 };
 
 __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
             acc = warp_sum(acc);
             if (lane == 0) a.part[(size_t)i * G + b] = acc;
         }
-        if (!tail_sync(a.bar, a.flag)) return;
+        if (!tail_sync(a.bar, a.flag, a.spin)) return;
         // dot i reduced by CTA i (fixed order over the CTA partials)
         for (int i = b; i < cnt; i += G) {
             double v = 0.0;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
             v = block_sum(v);
             if (tid == 0) hp[i] = v;
         }
-        if (!tail_sync(a.bar, a.flag)) return;
+        if (!tail_sync(a.bar, a.flag, a.spin)) return;
         for (int i = tid; i < cnt; i += TAIL_TPB) hs[i] = __ldcg(hp + i);
         __syncthreads();
         for (int e = e0 + tid; e < e1; e += TAIL_TPB) {
@@ -370,14 +371,14 @@ __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
     for (int e = e0 + tid; e < e1; e += TAIL_TPB) s2 = fma(a.w[e], a.w[e], s2);
     s2 = block_sum(s2);
     if (tid == 0) a.part[b] = s2;
-    if (!tail_sync(a.bar, a.flag)) return;
+    if (!tail_sync(a.bar, a.flag, a.spin)) return;
     if (b == 0) {
         double v = 0.0;
         for (int q = tid; q < G; q += TAIL_TPB) v += __ldcg(a.part + q);
         v = block_sum(v);
         if (tid == 0) *a.hn = sqrt(v);
     }
-    if (!tail_sync(a.bar, a.flag)) return;
+    if (!tail_sync(a.bar, a.flag, a.spin)) return;
     const double hn = __ldcg(a.hn);
     const double sc = hn > 0.0 ? 1.0 / hn : 0.0;
     for (int e = e0 + tid; e < e1; e += TAIL_TPB) a.Vnext[e] = a.w[e] * sc;
@@ -517,6 +518,7 @@ int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s)
         ta.n = n; ta.cnt = g.j + 1; ta.m = m;
         ta.bar = reinterpret_cast<TailBar *>(c->d_tailbar);
         ta.flag = c->d_flag;
+        ta.spin = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 24);
         void *args[] = {&ta};
         BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_arnoldi_tail, dim3(c->tail_grid),
                                                     dim3(TAIL_TPB), args, 0, s));
@@ -700,8 +702,9 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         return status;
     };
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-    // a barrier left half-way by a timed-out launch must not carry over
+    // a barrier left half-way, or sweep entries left, by a timed-out launch must not carry over
     BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_tailbar, 0, 2 * sizeof(unsigned int), s));
+    if ((rc = flow_reset(c, s))) return finish(rc);
     // arithmetic of the Newton residual and line search: the Krylov one while
     // |F| is large (refine_below > 0), the outer one for the final steps
     const int outer = c->opt.outer_precision;
