@@ -33,7 +33,12 @@ METRIC = "JFNK solve time & residual pair-evals/s at 181x61, mixed+learned vs pl
 UNIT = "pair-evals/s"
 # algorithmic work of the FP32C pair kernel per (target half point, source node)
 # index pair: 46 FP32 ALU instructions + 5 MUFU rsqrt = 51 issue slots
-INSTR_PER_INDEX_PAIR = 51
+INSTR_PER_INDEX_PAIR = 51  # 46 FP32 operations + 5 reciprocal square roots per index pair
+FP32_OPS_PER_INDEX_PAIR = 46
+MUFU_PER_INDEX_PAIR = 5  # reciprocal square roots per (target, source) index pair
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP32C pair-kernel launch at
+# 181x61 from an ncu capture of the current kernel; None until captured
+PAIRS_TRAFFIC = None
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP32 sweep launch at
 # 181x61 from an ncu capture of the current kernel; None until captured
 APPLY_TRAFFIC = None
@@ -50,6 +55,30 @@ def _peaks():
         with open(p) as fh:
             return json.load(fh), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def measure_alu_peaks(iters: int = 16384, reps: int = 5) -> dict:
+    """Roofline denominators of the pair kernels, measured on this GPU: the best
+    of `reps` launches of each pipe probe of the library (FP32 FMA: the issue
+    limit of FP32 work; FP32 rsqrt: the special-function unit; FP64 FMA),
+    timed with CUDA events on the launching stream, in tera lane-ops/s."""
+    import torch
+    from paper_1709_08803_gb300 import bfs
+    out = torch.empty(bfs.peak_probe_threads(), dtype=torch.float64, device="cuda")
+    res = {}
+    for kind, name, it in ((0, "ffma", iters), (1, "rsqrt", iters // 4), (2, "dfma", iters // 32),
+                           (3, "ffma2", iters)):
+        bfs.peak_probe(kind, it, out)
+        best = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = bfs.peak_probe(kind, it, out)
+            e1.record()
+            e1.synchronize()
+            best = max(best, ops / (e0.elapsed_time(e1) / 1e3))
+        res[name + "_tops"] = best / 1e12
+    return res
 
 
 class ClockSampler:
@@ -167,50 +196,67 @@ def run_reference(args):
     return 0
 
 
-def run_residual(args):
-    """Residual evaluations only (FP32C, then FP64) at 181 x 61: the pair-kernel
-    throughput part of the metric, with few launches before the first pair
-    kernel (the mode the kernel profiles are taken in)."""
+def residual_rates(mesh, topo, F, steps: int, warmup: int, precs=("fp32c", "df64", "fp64")) -> dict:
+    """Residual evaluations of one configuration in each arithmetic: time per
+    residual and per pair-kernel launch (CUDA events), pair-evals/s."""
     import torch
 
-    import __graft_entry__
     from paper_1709_08803_gb300 import bfs
     from paper_1709_08803_gb300 import workloads as W
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    __graft_entry__.build()
-    mesh, topo, F = W.config_paper_scale(args.F)
     ctx = bfs.Context(mesh, topo, F)
     u = torch.tensor(W.smooth_guess(mesh, 7), dtype=torch.float64, device="cuda")
     out = torch.empty_like(u)
+    code = {"fp32c": bfs.BFS_FP32C, "df64": bfs.BFS_DF64, "fp64": bfs.BFS_FP64}
     res = {}
-    for name, prec in (("fp32c", bfs.BFS_FP32C), ("df64", bfs.BFS_DF64), ("fp64", bfs.BFS_FP64)):
-        for _ in range(args.warmup):
+    for name in precs:
+        prec = code[name]
+        for _ in range(warmup):
             ctx.residual(u, out, precision=prec)
         torch.cuda.synchronize()
         ctx.profile_read()
         ctx.profile_enable(True)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             ctx.residual(u, out, precision=prec)
         ev1.record()
         ev1.synchronize()
         prof, _ = ctx.profile_read()
         ctx.profile_enable(False)
-        ms = ev0.elapsed_time(ev1) / args.steps
+        ms = ev0.elapsed_time(ev1) / steps
         kern = prof[name][0] / max(prof[name][1], 1)
         res[name] = {"residual_ms": ms, "pair_kernel_ms": kern,
                      "pair_evals_per_s": ctx.pair_evals / (ms / 1e3)}
-    peaks, src = _peaks()
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak = sms * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    ach = INSTR_PER_INDEX_PAIR * mesh.n_targets * mesh.n_sources / (res["fp32c"]["pair_kernel_ms"] / 1e3) / 1e12
-    print(json.dumps({"mode": "residual", "metric": "residual pair-evals/s at 181x61", "unit": UNIT,
+    ctx.close()
+    return res
+
+
+def run_residual(args):
+    """Residual evaluations only (FP32C, then double-float, then FP64) at 181 x 61
+    (or 361 x 121 with --config large): the pair-kernel throughput part of the
+    metric, with few launches before the first pair kernel (the mode the kernel
+    profiles are taken in)."""
+    import torch
+
+    import __graft_entry__
+    from paper_1709_08803_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    __graft_entry__.build()
+    mesh, topo, F = W.config_large() if args.config == "large" else W.config_paper_scale(args.F)
+    res = residual_rates(mesh, topo, F, args.steps, args.warmup)
+    alu = measure_alu_peaks()
+    peak = alu["ffma2_tops"]
+    pairs_per_s = mesh.n_targets * mesh.n_sources / (res["fp32c"]["pair_kernel_ms"] / 1e3)
+    ach = FP32_OPS_PER_INDEX_PAIR * pairs_per_s / 1e12
+    print(json.dumps({"mode": "residual", "metric": f"residual pair-evals/s at {mesh.N}x{mesh.M}", "unit": UNIT,
                       "value": res["fp32c"]["pair_evals_per_s"], "steps": args.steps, "warmup": args.warmup,
                       "results": res, "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
-                                                   "unit": "Tinst/s", "frac": ach / peak}}))
-    ctx.close()
+                                                   "unit": "T FP32 lane-ops/s", "frac": ach / peak,
+                                                   "peak_source": "measured packed FP32x2 FMA pipe probe",
+                                                   "mufu_frac": MUFU_PER_INDEX_PAIR * pairs_per_s / 1e12
+                                                   / alu["rsqrt_tops"],
+                                                   "measured_pipes": alu}}))
     return 0
 
 
@@ -357,12 +403,15 @@ def main():
                     help="storage/arithmetic of the preconditioner sweeps in the mixed form")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-large", action="store_true", help="skip the 361x121 residual throughput key")
     ap.add_argument("--no-learned", action="store_true",
                     help="time the solve from the uniform stream even when trained weights exist")
     ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch", "apply"],
                     help="solve: the JFNK step; residual: residual evaluations only; "
                          "batch: the 64-instance batched sweep")
     ap.add_argument("--batch", type=int, default=64, help="instances in --mode batch")
+    ap.add_argument("--config", default="paper", choices=["paper", "large"],
+                    help="--mode residual: 181x61 (paper) or 361x121 (large)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -556,15 +605,30 @@ def main():
     peaks, src = _peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak_tinst = sms * 128 * sm_mhz_max * 1e6 / 1e12
+    alu = measure_alu_peaks()
     avg32 = ms32 / max(n32, 1)
-    achieved = INSTR_PER_INDEX_PAIR * n_index_pairs / (avg32 / 1e3) / 1e12 if n32 else None
-    roofline_pairs = {"bound": "alu", "kernel": "k_pairs<float> (FP32C all-pairs quadrature)",
-                "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                "frac": (achieved / peak_tinst) if achieved else None,
+    pairs_per_s = n_index_pairs / (avg32 / 1e3) if n32 else None
+    # the binding pipe: the 46 FP32 operations of an index pair on the FMA pipe
+    # (128 lane-ops/clk/SM whether packed or not; packing only halves the issue
+    # slots), ahead of its 5 reciprocal square roots on the special-function
+    # unit (16 lanes/clk/SM)
+    achieved = FP32_OPS_PER_INDEX_PAIR * pairs_per_s / 1e12 if n32 else None
+    roofline_pairs = {"bound": "alu", "kernel": "k_pairs<float> (FP32C all-pairs quadrature, packed FP32x2)",
+                "achieved": achieved, "peak": alu["ffma2_tops"], "unit": "T FP32 lane-ops/s",
+                "frac": (achieved / alu["ffma2_tops"]) if achieved else None,
                 # dram bytes read + written per launch, from an ncu capture of this kernel at 181x61
-                "traffic": 1.43e6 if args.F == 0.7 else None,
-                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz (max SM clock, {src} peaks file)",
+                "traffic": PAIRS_TRAFFIC if args.F == 0.7 else None,
+                "peak_source": "measured: packed FP32x2 FMA throughput of the library's pipe probe on this "
+                               "GPU (best of 5 launches, CUDA events)",
+                "mufu": {"achieved": MUFU_PER_INDEX_PAIR * pairs_per_s / 1e12 if n32 else None,
+                         "peak": alu["rsqrt_tops"], "unit": "Trsqrt/s",
+                         "frac": (MUFU_PER_INDEX_PAIR * pairs_per_s / 1e12 / alu["rsqrt_tops"])
+                         if n32 else None,
+                         "peak_source": "measured rsqrtf throughput (pipe probe)"},
+                "peak_derived": sms * 128 * sm_mhz_max * 1e6 / 1e12,
+                "peak_derived_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_max:.0f} MHz "
+                                       f"(max SM clock, {src} peaks file)",
+                "measured_pipes": alu,
                 "avg_launch_ms": avg32, "launches": n32,
                 "fp64_pair_kernel_avg_ms": ms64 / max(n64, 1) if n64 else None,
                 "df64_pair_kernel_avg_ms": msdf / max(ndf, 1) if ndf else None,
@@ -606,6 +670,24 @@ def main():
                "sample": f"one full FP64 oracle residual at 181x61 ({mesh.pair_evals():.3e} pair "
                          f"evaluations, {dt:.2f} s)"}
 
+    # ---- the large configuration (361 x 121, 7.6e9 pair evaluations per
+    # residual): residual throughput beside the oracle's, outside the timed region
+    large = None
+    if rank == 0 and not args.no_large:
+        m5, t5, F5 = W.config_large()
+        r5 = residual_rates(m5, t5, F5, steps=5, warmup=2, precs=("fp32c", "df64"))
+        large = {"workload": "361x121 free surface + bottom, dx=dy=0.2, x in [-20,52], y in [-12,12], "
+                             "F=0.9, bump 0.3 exp(-(x^2+y^2)) + ridge 0.1 exp(-(x-5)^2/2)",
+                 "pair_evals_per_residual": m5.pair_evals(),
+                 "fp32c_pair_evals_per_s": r5["fp32c"]["pair_evals_per_s"],
+                 "fp32c_pair_kernel_ms": r5["fp32c"]["pair_kernel_ms"],
+                 "df64_pair_evals_per_s": r5["df64"]["pair_evals_per_s"]}
+        if not args.no_cpu:
+            rate5, cores5, dt5 = cpu_oracle_rate(m5, t5, F5, W.smooth_guess(m5, 7), reps=1)
+            large["oracle_pair_evals_per_s"] = rate5
+            large["oracle_cores"] = cores5
+            large["oracle_sample"] = f"one full FP64 oracle residual ({dt5:.2f} s)"
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -639,6 +721,7 @@ def main():
                 "step_breakdown": breakdown,
                 "roofline": roofline, "roofline_pairs": roofline_pairs, "roofline_apply": roofline_apply,
                 "cpu_baseline": cpu,
+                "large_361x121": large,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "entry": e2e_entry,
                         "ms_per_step": 1e3 * sum(e2e_times) / len(e2e_times), "steps": len(e2e_times)},

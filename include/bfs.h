@@ -109,7 +109,11 @@ typedef struct {
                               residual and the line search use the Krylov arithmetic
                               while |F|_inf > refine_below, then switch to
                               outer_precision for the final steps (iterative
-                              refinement); convergence is only ever accepted on an
+                              refinement); they switch earlier when a full Newton
+                              step in the Krylov arithmetic lowers |F|_2 by less
+                              than 10 % or its line search fails (the Krylov
+                              arithmetic's rounding then limits progress).
+                              Convergence is only ever accepted on an
                               outer_precision residual.  0 (default): always outer. */
     int stall_newton;      /* > 0: give up with BFS_ENOCONV once GMRES has ended above
                               its forcing tolerance (max_krylov reached) in this many
@@ -300,6 +304,19 @@ int bfs_debug_stall_sweep(bfs_ctx *ctx, int task);
 int bfs_profile_enable(bfs_ctx *ctx, int on);
 int bfs_profile_read(bfs_ctx *ctx, double *out8, unsigned long long *launches);
 
+/* Roofline probes (measurement only; the paper has no counterpart): one launch
+   of a kernel that streams a single instruction kind through its pipe with
+   no dependence between consecutive instructions and a full SM of warps:
+   kind 0 FP32 fused multiply-add, 1 FP32 reciprocal square root (the
+   special-function unit), 2 FP64 fused multiply-add, 3 packed FP32x2 fused
+   multiply-add (two lane operations per instruction).  out: DEVICE buffer of
+   bfs_peak_probe_threads() doubles (results kept live); *lane_ops receives
+   the lane operations the launch executes, so that lane_ops / (its CUDA-event
+   time) is the pipe's throughput.  Asynchronous on stream.  BFS_EINVAL for an
+   unknown kind, iters < 1 or out NULL. */
+int bfs_peak_probe(int kind, int iters, void *out, void *stream, double *lane_ops);
+int bfs_peak_probe_threads(void);
+
 /* Batched sweeps (an addition: the paper solves one problem at a
    time).  A batch holds B independent problems -- each its own mesh, bottom
    and Froude number -- and evaluates the FP32C residuals that their Krylov
@@ -340,8 +357,10 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
 /* Residual for callers that cannot allocate device memory.  The paper has no
    counterpart: this is a library convenience.  Code that runs where a device
    allocation is not allowed (inside a host callback, under a memory pool that
-   must not grow, or without ever creating a bfs_ctx) gets the same F(u) as
-   bfs_residual, from the same kernels, with every piece of scratch kept in one
+   must not grow, or without ever creating a bfs_ctx) gets the F(u) that
+   bfs_residual computes for a context with the default options (no surface
+   tension, no applied surface pressure), from the same kernels, with every
+   piece of scratch kept in one
    static device array of bfs_static_scratch_bytes() bytes (48 MiB) that each
    GPU loading the library holds until the process exits.  No cudaMalloc,
    cudaFree or allocating library routine is called.
@@ -356,7 +375,8 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
    N*M <= 60000 nodes); BFS_ECUDA if the device address of the array cannot
    be obtained.  The first call on each device looks that address up (with the
    device current) and caches it: make that first call before any stream
-   capture.  All calls share the array, which keeps the last call's contents
+   capture, and do not use this entry point across a cudaDeviceReset of the
+   device (the cached address belongs to the context the reset destroys).  All calls share the array, which keeps the last call's contents
    (the NaN flag is cleared on entry; nothing else needs clearing): calls
    that overlap on the GPU (unordered streams) race and give wrong results;
    calls ordered in one stream are safe.  A non-finite result is not reported

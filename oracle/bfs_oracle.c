@@ -100,6 +100,9 @@ void orc_set_threads(int n)
 
 static int orc_n(const orc_problem *P) { return 3 * (P->N + 1) * P->M; }
 
+int orc_lu_factor(int n, double *A, int *piv);
+void orc_lu_solve(int n, const double *LU, const int *piv, const double *b, double *x);
+
 /* ------------------------------------------------------------------ */
 /* Unknown vector -> nodal values (Sec. 3.1, the vector of unknowns).          */
 /* Per slice j and field q: u holds q(x1, y_j) followed by q_x at the   */
@@ -538,6 +541,205 @@ void orc_jtilde(const orc_problem *P, int half_band, double *J)
     free(e); free(F0); free(Fc);
 }
 
+/* ------------------------------------------------------------------ */
+/* Banded linear Jacobian, block by block (Sec. 4.2 with the banding of */
+/* App. A), for meshes whose dense J~ does not fit in memory.           */
+/* ------------------------------------------------------------------ */
+/*
+ * Unknowns and equations regrouped slice by slice: slice l owns the
+ * nb = 3(N+1) equations [F5, F6, F1(1..N-1) | F3, F4, F2(1..N-1) | F8, F9,
+ * F7(1..N-1)] and the nb unknowns [zeta(1), zeta_x(1..N) | phi(1), phi_x |
+ * psi(1), psi_x] of that slice, i.e. the rows and columns of J~ with slice
+ * index l, in the order they have in F and in u.  Block (l, m), |l - m| <= h,
+ * is stored at Bk + (l (2h+1) + m - l + h) nb^2, row-major.
+ *
+ * The linear system is affine in u, so column c of J~ is the change of the
+ * linear residual of orc_residual_linear when unknown c goes from 0 to 1
+ * (the constants of f = phi - x, g = psi - x, the -1 of the dynamic condition
+ * and of the radiation conditions cancel).  That unknown changes the nodal
+ * values of its own slice m only (the trapezoid rule acts along x; the linear
+ * residual uses no y-derivative), so the change of each sum over sources
+ * comes from the sources of slice m and, in the half domain, their mirror
+ * images; the target's own half-point values enter only the rows of slice m.
+ * Surface tension, whose curvature term couples slices, is not supported.
+ */
+int orc_jtilde_band(const orc_problem *P, int h, double *Bk)
+{
+    int N = P->N, M = P->M, NB = N + 1, nb = 3 * NB, nd = 2 * h + 1;
+    size_t bsz = (size_t)nb * nb;
+    if (P->tau != 0.0 || h < 0) return -1;
+    memset(Bk, 0, (size_t)M * nd * bsz * sizeof(double));
+    double ylo = P->half ? -(P->y1 + (M - 1) * P->dy) : P->y1;
+    double yhi = P->y1 + (M - 1) * P->dy, xhi = P->x1 + (N - 1) * P->dx;
+    int nt = (N - 1) * M;
+    /* per target: sum over all sources of w K5 (the subtraction of zeta_x*)
+       and the closed-form integral of K5 over the truncated domain */
+    double *R5 = (double *)malloc((size_t)nt * sizeof(double));
+    double *I5 = (double *)malloc((size_t)nt * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int e = 0; e < nt; e++) {
+        int k = e % (N - 1), l = e / (N - 1);
+        double xs = P->x1 + (k + 0.5) * P->dx, ys = P->y1 + l * P->dy, acc = 0.0;
+        for (int img = 0; img < (P->half ? 2 : 1); img++)
+            for (int j = 0; j < M; j++) {
+                if (img && j == 0) continue;
+                double yj = (img ? -1.0 : 1.0) * (P->y1 + j * P->dy);
+                for (int i = 0; i < N; i++) {
+                    double s = P->x1 + i * P->dx - xs, t = yj - ys;
+                    acc += orc_weight(P, i, j) / sqrt(s * s + t * t);
+                }
+            }
+        R5[e] = acc;
+        I5[e] = orc_rect_S2(1.0, 0.0, 1.0, P->x1 - xs, xhi - xs, ylo - ys, yhi - ys);
+    }
+#pragma omp parallel
+    {
+        double *e = (double *)calloc((size_t)orc_n(P), sizeof(double));
+        double *q = (double *)malloc((size_t)N * M * sizeof(double));
+        double *qx = (double *)malloc((size_t)N * M * sizeof(double));
+#pragma omp for schedule(dynamic, 8)
+        for (int col = 0; col < M * nb; col++) {
+            int m = col / nb, cl = col % nb, g = cl / NB, p = cl % NB;
+            size_t uc = (size_t)g * NB * M + (size_t)m * NB + p; /* index in u */
+            e[uc] = 1.0;
+            orc_unpack_field(P, e, g, q, qx); /* nodal change of field g (slice m only) */
+            e[uc] = 0.0;
+            const double *dq = q + (size_t)m * N, *dqx = qx + (size_t)m * N;
+            /* per field: zeta enters through zeta_x (K5 top, K7 bottom targets) and
+               zeta (dynamic condition); phi through f (K6 at bottom targets) and
+               phi_x (dynamic condition); psi through g (K6 at top targets) */
+            for (int l = (m - h > 0 ? m - h : 0); l <= (m + h < M - 1 ? m + h : M - 1); l++) {
+                double *blk = Bk + ((size_t)l * nd + (m - l + h)) * bsz;
+                for (int k = 0; k < N - 1; k++) {
+                    double xs = P->x1 + (k + 0.5) * P->dx, ys = P->y1 + l * P->dy;
+                    double s2 = 0.0, s7 = 0.0;
+                    for (int img = 0; img < (P->half ? 2 : 1); img++) {
+                        if (img && m == 0) continue;
+                        double yj = (img ? -1.0 : 1.0) * (P->y1 + m * P->dy);
+                        for (int i = 0; i < N; i++) {
+                            double w = orc_weight(P, i, m);
+                            double s = P->x1 + i * P->dx - xs, t = yj - ys, r2 = s * s + t * t;
+                            double K5 = 1.0 / sqrt(r2), K7 = 1.0 / sqrt(r2 + 1.0), K6 = K7 * K7 * K7;
+                            if (g == 0) { s2 += w * dqx[i] * K5; s7 += w * dqx[i] * K7; }
+                            else if (g == 1) s7 += w * dq[i] * K6;
+                            else s2 += w * dq[i] * K6;
+                        }
+                    }
+                    double F1 = 0.0, F2 = s2, F7 = s7;
+                    if (l == m) { /* the target's own half-point values */
+                        double hq = 0.5 * (dq[k] + dq[k + 1]), hqx = 0.5 * (dqx[k] + dqx[k + 1]);
+                        int et = l * (N - 1) + k;
+                        if (g == 0) { F1 = hq / (P->F * P->F); F2 += hqx * (I5[et] - R5[et]); }
+                        else if (g == 1) { F1 = hqx; F2 -= 2.0 * ORC_PI * hq; }
+                        else F7 -= 2.0 * ORC_PI * hq;
+                    }
+                    blk[(size_t)(0 * NB + 2 + k) * nb + cl] = F1;
+                    blk[(size_t)(1 * NB + 2 + k) * nb + cl] = F2;
+                    blk[(size_t)(2 * NB + 2 + k) * nb + cl] = F7;
+                }
+                if (l == m) { /* radiation rows of slice m: their linear parts */
+                    double x1 = P->x1, n = P->n_rad, hx = P->dx;
+                    double v1 = dq[0], d1 = dqx[0], d2 = dqx[1];
+                    blk[(size_t)(g * NB + 0) * nb + cl] = x1 * d1 + n * v1;
+                    blk[(size_t)(g * NB + 1) * nb + cl] = x1 * (d2 - d1) / hx + n * d1;
+                }
+            }
+        }
+        free(e); free(q); free(qx);
+    }
+    free(R5); free(I5);
+    return 0;
+}
+
+/*
+ * In-place block LU of the banded matrix (App. A: no pivoting across blocks,
+ * partial pivoting inside each diagonal block):
+ *   for k = 0..M-1:  D_k = B(k,k) = Pi L U (orc_lu_factor, pivots at piv + k nb);
+ *     B(k,j) <- D_k^-1 B(k,j)          for j = k+1..k+h
+ *     B(i,j) <- B(i,j) - B(i,k) B(k,j)  for i, j = k+1..k+h
+ * Returns -1 on a zero pivot.
+ */
+int orc_band_factor(int M, int nb, int h, double *Bk, int *piv)
+{
+    int nd = 2 * h + 1;
+    size_t bsz = (size_t)nb * nb;
+#define ORC_B(l, m) (Bk + ((size_t)(l) * nd + ((m) - (l) + h)) * bsz)
+    double *col = (double *)malloc((size_t)nb * sizeof(double));
+    for (int k = 0; k < M; k++) {
+        double *D = ORC_B(k, k);
+        if (orc_lu_factor(nb, D, piv + (size_t)k * nb)) { free(col); return -1; }
+        int hi = k + h < M - 1 ? k + h : M - 1;
+        for (int j = k + 1; j <= hi; j++) {
+            double *U = ORC_B(k, j);
+            for (int c = 0; c < nb; c++) {
+                for (int r = 0; r < nb; r++) col[r] = U[(size_t)r * nb + c];
+                orc_lu_solve(nb, D, piv + (size_t)k * nb, col, col);
+                for (int r = 0; r < nb; r++) U[(size_t)r * nb + c] = col[r];
+            }
+        }
+        for (int i = k + 1; i <= hi; i++)
+            for (int j = k + 1; j <= hi; j++) {
+                const double *L = ORC_B(i, k), *U = ORC_B(k, j);
+                double *S = ORC_B(i, j);
+#pragma omp parallel for schedule(static)
+                for (int r = 0; r < nb; r++)
+                    for (int t = 0; t < nb; t++) {
+                        double a = L[(size_t)r * nb + t];
+                        if (a != 0.0)
+                            for (int c = 0; c < nb; c++) S[(size_t)r * nb + c] -= a * U[(size_t)t * nb + c];
+                    }
+            }
+    }
+    free(col);
+    return 0;
+}
+
+/*
+ * z = P^-1 r with the factors of orc_band_factor; r in the order of F, z in
+ * the order of u (both regrouped by slice inside):
+ *   forward  w_k = D_k^-1 (r_k - sum_{i=k-h}^{k-1} B(k,i) w_i)
+ *   backward z_k = w_k - sum_{j=k+1}^{k+h} B(k,j) z_j
+ */
+void orc_band_solve(int N, int M, int h, const double *Bk, const int *piv, const double *r, double *z)
+{
+    int NB = N + 1, nb = 3 * NB, nd = 2 * h + 1;
+    size_t bsz = (size_t)nb * nb;
+    double *w = (double *)malloc((size_t)M * nb * sizeof(double));
+    for (int l = 0; l < M; l++)
+        for (int g = 0; g < 3; g++)
+            for (int p = 0; p < NB; p++)
+                w[(size_t)l * nb + g * NB + p] = r[(size_t)g * NB * M + (size_t)l * NB + p];
+    for (int k = 0; k < M; k++) {
+        double *wk = w + (size_t)k * nb;
+        for (int i = (k - h > 0 ? k - h : 0); i < k; i++) {
+            const double *L = ORC_B(k, i), *wi = w + (size_t)i * nb;
+            for (int a = 0; a < nb; a++) {
+                double s = 0.0;
+                for (int b = 0; b < nb; b++) s += L[(size_t)a * nb + b] * wi[b];
+                wk[a] -= s;
+            }
+        }
+        orc_lu_solve(nb, ORC_B(k, k), piv + (size_t)k * nb, wk, wk);
+    }
+    for (int k = M - 1; k >= 0; k--) {
+        double *zk = w + (size_t)k * nb;
+        for (int j = k + 1; j <= (k + h < M - 1 ? k + h : M - 1); j++) {
+            const double *U = ORC_B(k, j), *zj = w + (size_t)j * nb;
+            for (int a = 0; a < nb; a++) {
+                double s = 0.0;
+                for (int b = 0; b < nb; b++) s += U[(size_t)a * nb + b] * zj[b];
+                zk[a] -= s;
+            }
+        }
+    }
+    for (int l = 0; l < M; l++)
+        for (int g = 0; g < 3; g++)
+            for (int p = 0; p < NB; p++)
+                z[(size_t)g * NB * M + (size_t)l * NB + p] = w[(size_t)l * nb + g * NB + p];
+    free(w);
+#undef ORC_B
+}
+
 /* Finite-difference Jacobian of F (column c: (F(u + h e_c) - F(u)) / h). */
 void orc_fd_jacobian(const orc_problem *P, const double *beta, const double *bx,
                      const double *by, const double *u, double *J)
@@ -629,6 +831,7 @@ typedef struct {
     const double *LU; const int *piv; /* preconditioner P = LU (dense) or NULL */
     int n, evals;
     double *tmp_u, *tmp_F;
+    const double *Bk; const int *bpiv; int h; /* or the banded block LU of orc_band_factor */
 } orc_ctx;
 
 static void orc_eval(orc_ctx *c, const double *u, double *Fv)
@@ -640,6 +843,7 @@ static void orc_eval(orc_ctx *c, const double *u, double *Fv)
 static void orc_prec(orc_ctx *c, const double *r, double *z)
 {
     if (c->LU) orc_lu_solve(c->n, c->LU, c->piv, r, z);
+    else if (c->Bk) orc_band_solve(c->P->N, c->P->M, c->h, c->Bk, c->bpiv, r, z);
     else if (z != r) memcpy(z, r, (size_t)c->n * sizeof(double));
 }
 
@@ -733,8 +937,10 @@ static int orc_gmres(orc_ctx *c, const double *u, const double *Fu, double eta, 
 
 /*
  * Damped inexact Newton with backtracking line search (Sec. 3.2).
- * half_band < 0 means the full linear Jacobian J~ as preconditioner; >= 0
- * its banded form; a value of -2 means no preconditioner.  Returns 0 when
+ * half_band = -1 means the full linear Jacobian J~ as preconditioner; >= 0
+ * its banded form (dense storage); -2 no preconditioner; -3 - h the banded
+ * form with half band h in block storage, factored by orc_band_factor (for
+ * meshes whose dense J~ does not fit in memory).  Returns 0 when
  * |F|_inf <= tol, 1 when the iteration limit is reached, 2 when the line
  * search fails, 3 on a singular preconditioner.
  */
@@ -743,13 +949,20 @@ int orc_jfnk(const orc_problem *P, const double *beta, const double *bx, const d
              int max_krylov, double eta, orc_stats *st)
 {
     int n = orc_n(P);
-    orc_ctx c = {P, beta, bx, by, NULL, NULL, n, 0, NULL, NULL};
+    orc_ctx c = {P, beta, bx, by, NULL, NULL, n, 0, NULL, NULL, NULL, NULL, 0};
     c.tmp_u = (double *)malloc((size_t)n * sizeof(double));
     c.tmp_F = (double *)malloc((size_t)n * sizeof(double));
     double *LU = NULL; int *piv = NULL;
     int status = 1;
     memset(st, 0, sizeof(*st));
-    if (half_band != -2) {
+    if (half_band <= -3) {
+        /* banded block LU (orc_jtilde_band + orc_band_factor), half band -3 - half_band */
+        int h = -3 - half_band, nb = 3 * (P->N + 1);
+        LU = (double *)malloc((size_t)P->M * (2 * h + 1) * nb * nb * sizeof(double));
+        piv = (int *)malloc((size_t)P->M * nb * sizeof(int));
+        if (orc_jtilde_band(P, h, LU) || orc_band_factor(P->M, nb, h, LU, piv)) { status = 3; goto done; }
+        c.Bk = LU; c.bpiv = piv; c.h = h;
+    } else if (half_band != -2) {
         LU = (double *)malloc((size_t)n * n * sizeof(double));
         piv = (int *)malloc((size_t)n * sizeof(int));
         orc_jtilde(P, half_band < 0 ? -1 : half_band, LU);

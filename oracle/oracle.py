@@ -14,6 +14,10 @@ Parity status of each function (how it is pinned, see tests/test_oracle_pins.py)
   residual_linear / jtilde ... App. B printed entries that are self-consistent,
                        block symmetries J23 = J32, J22 = J33 (Sec. 4.2)
   lu / jfnk / newton_dense ... dense solve vs numpy; JFNK vs dense FD Newton
+  jtilde_band ........ every stored block equals the band of the dense J~
+                       (full and half domain)
+  band_factor/solve .. the banded block LU solves the banded J~ as the dense
+                       LU does; JFNK with it reaches the dense-LU root
   bottom_pressure .... hydrostatic value at the uniform stream; Bernoulli on a
                        streamsurface of a linear potential; force = 0 with
                        no bottom slope
@@ -86,6 +90,9 @@ def lib():
             L.orc_residual.argtypes = [P, _D, _D, _D, _D, _D, _D]
             L.orc_residual_linear.argtypes = [P, _D, _D, _D]
             L.orc_jtilde.argtypes = [P, ctypes.c_int, _D]
+            L.orc_jtilde_band.argtypes = [P, ctypes.c_int, _D]
+            L.orc_band_factor.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]
+            L.orc_band_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I, _D, _D]
             L.orc_fd_jacobian.argtypes = [P, _D, _D, _D, _D, _D]
             L.orc_nodal_values.argtypes = [P, _D, _D]
             L.orc_rect_S2.argtypes = [ctypes.c_double] * 7
@@ -164,6 +171,34 @@ def jtilde(P: Problem, half_band: int = -1) -> np.ndarray:
     return J
 
 
+def jtilde_band(P: Problem, half_band: int) -> np.ndarray:
+    """Blocks (l, m), |l - m| <= half_band, of J~ regrouped slice by slice:
+    array (M, 2 half_band + 1, nb, nb), block (l, m) at [l, m - l + half_band]."""
+    nb = 3 * (P.N + 1)
+    B = np.empty((P.M, 2 * half_band + 1, nb, nb))
+    if lib().orc_jtilde_band(ctypes.byref(P), int(half_band), _p(B)):
+        raise ValueError("banded J~ needs tau = 0 and half_band >= 0")
+    return B
+
+
+def band_factor(P: Problem, B: np.ndarray):
+    """Block LU of jtilde_band's blocks in place; returns the pivots."""
+    nb = 3 * (P.N + 1)
+    h = (B.shape[1] - 1) // 2
+    piv = np.empty(P.M * nb, dtype=np.int32)
+    if lib().orc_band_factor(P.M, nb, h, _p(B), piv.ctypes.data_as(_I)):
+        raise ZeroDivisionError("singular diagonal block")
+    return piv
+
+
+def band_solve(P: Problem, B: np.ndarray, piv: np.ndarray, r) -> np.ndarray:
+    """z = P^-1 r with band_factor's factors (r in the order of F, z of u)."""
+    h = (B.shape[1] - 1) // 2
+    z = np.empty(3 * (P.N + 1) * P.M)
+    lib().orc_band_solve(P.N, P.M, h, _p(B), piv.ctypes.data_as(_I), _p(_f64(r)), _p(z))
+    return z
+
+
 def fd_jacobian(P: Problem, topo, u) -> np.ndarray:
     n = 3 * (P.N + 1) * P.M
     J = np.empty((n, n))
@@ -224,12 +259,19 @@ def lu_solve_dense(A: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 
 def jfnk(P: Problem, topo, u0, half_band: int = -1, tol: float = 1e-10, max_newton: int = 50,
-         restart: int = 50, max_krylov: int = 400, eta: float = 1e-4):
-    """Damped JFNK solve from u0; returns (u, stats dict)."""
+         restart: int = 50, max_krylov: int = 400, eta: float = 1e-4, banded: bool = False):
+    """Damped JFNK solve from u0; returns (u, stats dict).  banded=True takes
+    the banded preconditioner in block storage (half_band >= 0), for meshes
+    whose dense J~ does not fit in memory."""
     u = _f64(u0).copy()
     b, bx, by = _f64(topo.beta), _f64(topo.beta_x), _f64(topo.beta_y)
     st = Stats()
-    lib().orc_jfnk(ctypes.byref(P), _p(b), _p(bx), _p(by), _p(u), int(half_band), tol,
+    hb = int(half_band)
+    if banded:
+        if hb < 0:
+            raise ValueError("banded preconditioner needs half_band >= 0")
+        hb = -3 - hb
+    lib().orc_jfnk(ctypes.byref(P), _p(b), _p(bx), _p(by), _p(u), hb, tol,
                    max_newton, restart, max_krylov, eta, ctypes.byref(st))
     return u, st.as_dict()
 

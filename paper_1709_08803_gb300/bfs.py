@@ -130,6 +130,7 @@ def lib():
                                          ctypes.c_int, C(ctypes.c_int)]
         L.bfs_debug_stall_sweep.argtypes = [_VP, ctypes.c_int]
         L.bfs_precond_info.argtypes = [_VP, C(ctypes.c_int)]
+        L.bfs_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _VP, _VP, C(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -372,6 +373,22 @@ def sweep_schedule(M: int, half_band: int, twisted: bool):
     if n2 != n:
         raise BfsError(n2, "sweep schedule changed between calls")
     return np.frombuffer(buf, dtype=np.int32, count=16 * n).reshape(n, 16).copy(), (cnt[0], cnt[1])
+
+
+def peak_probe(kind: int, iters: int, out, stream=None) -> float:
+    """Launch one roofline probe (0 FP32 FMA, 1 FP32 rsqrt, 2 FP64 FMA) writing
+    into the device tensor `out` (peak_probe_threads() float64 entries);
+    returns the lane operations the launch executes."""
+    ops = ctypes.c_double()
+    rc = lib().bfs_peak_probe(int(kind), int(iters), ctypes.c_void_p(out.data_ptr()), _stream(stream),
+                              ctypes.byref(ops))
+    if rc:
+        raise BfsError(rc, "peak probe failed")
+    return ops.value
+
+
+def peak_probe_threads() -> int:
+    return int(lib().bfs_peak_probe_threads())
 
 
 class Batch:

@@ -12,6 +12,8 @@
 //              term, the combined dynamic condition and the radiation rows
 #include <math.h>
 
+#include <algorithm>
+
 #include "bfs_internal.cuh"
 
 namespace bfs {
@@ -292,13 +294,186 @@ __device__ __forceinline__ void pair_tile(const R *__restrict__ src, int per_spl
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32C all-pairs with the packed FP32x2 arithmetic of sm_100-class GPUs: one
+// instruction applies the same operation to two sources, so the 46 FP32
+// operations of an index pair take 23 issue slots (the five reciprocal square
+// roots stay scalar on the special-function unit).  Sources are staged in
+// shared memory as interleaved pairs (value v of sources 2i and 2i+1 side by
+// side, one 64-bit word), the target values are broadcast into both halves
+// once per tile, and the offsets are taken target minus source so that no
+// operand needs a negation; the density w g of the bottom double layer is
+// negated while staging for the same reason.  The sums are those of
+// pair_tile<float>: each half accumulates its sources over a chunk, the halves
+// are added and the chunk total enters the two-sum accumulator.
+// ---------------------------------------------------------------------------
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_pack(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 x, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 f2_rsq(f2 x)
+{
+    float a, b;
+    f2_unpack(x, a, b);
+    return f2_pack(rsqrtf(a), rsqrtf(b));
+}
+
+template <int TPB, int TPT, int CH>
+__device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int per_split,
+                                             const float *__restrict__ tgt, int Nt,
+                                             double *__restrict__ part, int tile, int split, float *sh)
+{
+    static_assert(CH % 2 == 0, "sources are taken in pairs");
+    const float *sb = src + (size_t)split * per_split * REC;
+    // target values broadcast into both halves; -f* for the top double layer
+    f2 TX[TPT], TY[TPT], TZ[TPT], TB[TPT], NTF[TPT], TG[TPT], CA[TPT], CB[TPT], CC[TPT], CTB[TPT], CBT[TPT];
+    int tid[TPT];
+#pragma unroll
+    for (int p = 0; p < TPT; p++) {
+        int t = tile * TPB * TPT + p * TPB + threadIdx.x;
+        tid[p] = t;
+        const float *tr = tgt + (size_t)min(t, Nt - 1) * TREC;
+        TX[p] = f2_pack(tr[0], tr[0]); TY[p] = f2_pack(tr[1], tr[1]);
+        TZ[p] = f2_pack(tr[2], tr[2]); TB[p] = f2_pack(tr[3], tr[3]);
+        NTF[p] = f2_pack(-tr[6], -tr[6]); TG[p] = f2_pack(tr[7], tr[7]);
+        CA[p] = f2_pack(tr[8], tr[8]); CB[p] = f2_pack(tr[9], tr[9]); CC[p] = f2_pack(tr[10], tr[10]);
+        CTB[p] = f2_pack(tr[11], tr[11]); CBT[p] = f2_pack(tr[12], tr[12]);
+    }
+    float hi[TPT][NACC], lo[TPT][NACC];
+#pragma unroll
+    for (int p = 0; p < TPT; p++)
+#pragma unroll
+        for (int q = 0; q < NACC; q++) { hi[p][q] = 0.f; lo[p][q] = 0.f; }
+
+    const f2 *sp2 = reinterpret_cast<const f2 *>(sh);
+    for (int c0 = 0; c0 < per_split; c0 += CH) {
+        __syncthreads();
+        // stage the chunk as interleaved source pairs: value v of source s at
+        // 2 ((s / 2) REC + v) + (s & 1); w g (value 10) negated
+        const float4 *g = reinterpret_cast<const float4 *>(sb + (size_t)c0 * REC);
+        for (int e = threadIdx.x; e < CH * REC / 4; e += TPB) {
+            const float4 v4 = g[e];
+            const int s = e / (REC / 4), v0 = (e - s * (REC / 4)) * 4;
+            float *d = sh + 2 * ((s >> 1) * REC + v0) + (s & 1);
+            d[0] = v4.x;
+            d[2] = v4.y;
+            d[4] = v0 + 2 == 10 ? -v4.z : v4.z;
+            d[6] = v4.w;
+        }
+        __syncthreads();
+        f2 L[TPT][NACC];
+#pragma unroll
+        for (int p = 0; p < TPT; p++)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) L[p][q].v = 0ull;
+#pragma unroll 2
+        for (int i = 0; i < CH / 2; i++) {
+            const f2 *r = sp2 + i * REC;
+            const f2 xs = r[0], ys = r[1], zs = r[2], bs = r[3];
+            const f2 zxs = r[4], zys = r[5], bxs = r[6], bys = r[7];
+            const f2 w1f = r[8], w2zx = r[9], nw1g = r[10], w2sb = r[11];
+            const f2 w1 = r[12], w2 = r[13];
+#pragma unroll
+            for (int p = 0; p < TPT; p++) {
+                const f2 sx = f2_sub(TX[p], xs), sy = f2_sub(TY[p], ys);  // target minus source
+                const f2 syy = f2_mul(sy, sy);
+                const f2 rho2 = f2_fma(sx, sx, syy);
+                // top target, top source: w (f - f*) K1 + w zeta_x K2, and w S2
+                {
+                    const f2 d = f2_sub(zs, TZ[p]);
+                    const f2 ri = f2_rsq(f2_fma(d, d, rho2));
+                    const f2 ri3 = f2_mul(f2_mul(ri, ri), ri);
+                    const f2 num = f2_fma(sy, zys, f2_fma(sx, zxs, d));
+                    const f2 dens = f2_fma(NTF[p], w1, w1f);
+                    L[p][0] = f2_fma(f2_mul(dens, num), ri3, L[p][0]);
+                    L[p][1] = f2_fma(w2zx, ri, L[p][1]);
+                    const f2 qf = f2_fma(sx, f2_fma(CA[p], sx, f2_mul(CB[p], sy)), f2_mul(CC[p], syy));
+                    L[p][2] = f2_fma(w2, f2_rsq(qf), L[p][2]);
+                }
+                // top target, bottom source: -w g K1(beta) + w sigma beta_x K2(beta)
+                {
+                    const f2 d = f2_sub(bs, CTB[p]);
+                    const f2 ri = f2_rsq(f2_fma(d, d, rho2));
+                    const f2 ri3 = f2_mul(f2_mul(ri, ri), ri);
+                    const f2 num = f2_fma(sy, bys, f2_fma(sx, bxs, d));
+                    L[p][0] = f2_fma(f2_mul(nw1g, num), ri3, L[p][0]);
+                    L[p][1] = f2_fma(w2sb, ri, L[p][1]);
+                }
+                // bottom target, top source: w f K1 + w zeta_x K2
+                {
+                    const f2 d = f2_sub(zs, CBT[p]);
+                    const f2 ri = f2_rsq(f2_fma(d, d, rho2));
+                    const f2 ri3 = f2_mul(f2_mul(ri, ri), ri);
+                    const f2 num = f2_fma(sy, zys, f2_fma(sx, zxs, d));
+                    L[p][3] = f2_fma(f2_mul(w1f, num), ri3, L[p][3]);
+                    L[p][4] = f2_fma(w2zx, ri, L[p][4]);
+                }
+                // bottom target, bottom source: -w (g - g*) K1(beta)
+                {
+                    const f2 d = f2_sub(bs, TB[p]);
+                    const f2 ri = f2_rsq(f2_fma(d, d, rho2));
+                    const f2 ri3 = f2_mul(f2_mul(ri, ri), ri);
+                    const f2 num = f2_fma(sy, bys, f2_fma(sx, bxs, d));
+                    const f2 densn = f2_fma(TG[p], w1, nw1g);  // g* w - w g
+                    L[p][3] = f2_fma(f2_mul(densn, num), ri3, L[p][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < TPT; p++)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) {
+                float a, b;
+                f2_unpack(L[p][q], a, b);
+                two_sum_acc(hi[p][q], lo[p][q], a + b);
+            }
+    }
+#pragma unroll
+    for (int p = 0; p < TPT; p++) {
+        if (tid[p] >= Nt) continue;
+#pragma unroll
+        for (int q = 0; q < NACC; q++)
+            part[((size_t)split * NACC + q) * Nt + tid[p]] = (double)hi[p][q] + (double)lo[p][q];
+    }
+}
+
 template <typename R, int TPB, int TPT, int CH, bool COMP>
 __global__ void __launch_bounds__(TPB)
 k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int Nt,
         double *__restrict__ part)
 {
     __shared__ __align__(16) R sh[CH * REC];
-    pair_tile<R, TPB, TPT, CH, COMP>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, sh);
+    if constexpr (sizeof(R) == 4 && COMP)
+        pair_tile_x2<TPB, TPT, CH>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, sh);
+    else
+        pair_tile<R, TPB, TPT, CH, COMP>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,6 +685,10 @@ static FinArgs fin_args(const bfs_ctx *c, int splits)
     return a;
 }
 
+// Source splits of a pair-kernel launch: about eight CTAs' worth of (target
+// tile, source split) items per SM, small enough that the block scheduler,
+// refilling each SM as its CTAs finish, evens out the load.  splits_req > 0
+// asks for a split count instead.
 PairPlan make_plan(int Nt, int Ns, int tpb, int tpt, int chunk, int splits_req, int sms)
 {
     PairPlan p;
@@ -608,8 +787,7 @@ k_pairs_batch(const BatchInst *__restrict__ inst, const int4 *__restrict__ items
         const int4 item = items[w];
         if (!mask[item.x]) continue;
         const BatchInst I = inst[item.x];
-        pair_tile<float, TPB, TPT, P32_CH, true>(I.src, I.per_split, I.tgt, I.Nt, I.part, item.y,
-                                                 item.z, sh);
+        pair_tile_x2<TPB, TPT, P32_CH>(I.src, I.per_split, I.tgt, I.Nt, I.part, item.y, item.z, sh);
     }
 }
 

@@ -722,7 +722,7 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
     // forcing terms (Eisenstat-Walker choice 1 when opt.forcing == 1)
     const double eta_min = c->opt.eta;
     double eta_k = c->opt.forcing == 1 ? std::max(eta_min, 0.1) : eta_min;
-    double prev_f2 = -1.0, prev_lin = 0.0;
+    double prev_f2 = -1.0, prev_lin = 0.0, last_mu = 0.0;
     for (int k = 0;; k++) {
         if (c->opt.forcing == 1 && prev_f2 > 0.0) {
             const double prev_eta = eta_k;
@@ -731,7 +731,13 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             if (sg > 0.1) e = std::max(e, sg);
             eta_k = std::min(0.9, std::max(eta_min, e));
         }
-        if (cur != outer && isfinite(finf) && (finf <= c->opt.refine_below || finf <= c->opt.tol)) {
+        // switch to the outer arithmetic for the final steps: below refine_below,
+        // at the tolerance, or when a full Newton step in the Krylov arithmetic
+        // reduced |F|_2 by less than 10 % (its rounding, not the linearisation,
+        // then limits progress)
+        const bool stagnant = prev_f2 > 0.0 && last_mu == 1.0 && f2 > 0.9 * prev_f2;
+        if (cur != outer && isfinite(finf) &&
+            (finf <= c->opt.refine_below || finf <= c->opt.tol || stagnant)) {
             if ((rc = residual_launch(c, u, c->d_F, outer, s))) return finish(rc);
             count(outer);
             norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
@@ -793,8 +799,22 @@ int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             }
             mu *= 0.5;
         }
-        if (!ok) return finish(BFS_ELINESEARCH);
+        if (!ok) {
+            if (cur == outer) return finish(BFS_ELINESEARCH);
+            // no sufficient decrease in the Krylov arithmetic: its rounding is the
+            // limit; continue with the outer arithmetic from the same iterate
+            if ((rc = residual_launch(c, u, c->d_F, outer, s))) return finish(rc);
+            count(outer);
+            norms_launch(c, c->d_F, n, c->d_scal + 10, c->d_scal + 11, s);
+            if ((rc = read_scalars(c, c->d_scal + 10, 2, s))) return finish(rc);
+            f2 = c->h_pin[0];
+            finf = c->h_pin[1];
+            cur = outer;
+            prev_f2 = -1.0;
+            continue;
+        }
         // |F + J (mu du)| estimated from the GMRES residual of the full step
+        last_mu = mu;
         prev_f2 = f2;
         prev_lin = (1.0 - mu) * f2 + mu * gk.res;
         f2 = c->h_pin[0];

@@ -10,11 +10,16 @@
 // g_static_scratch, of BFS_STATIC_SCRATCH_BYTES bytes.  Every GPU that loads
 // the library holds that array until the process exits.
 //
+// The residual is the one of a context with the default options: no surface
+// tension and no applied surface pressure.
+//
 // In host code the name g_static_scratch is only a host-side stand-in for
 // the symbol, not a device address; its device address is looked up once per
 // device (cudaGetSymbolAddress, with that device current) on the first call
 // on that device, and cached.  That first call should therefore come before
-// any stream capture.  All calls share the one array: calls whose work
+// any stream capture.  The cached address belongs to the device's current
+// primary context: after a cudaDeviceReset of that device it is stale, so the
+// entry point must not be used across a reset.  All calls share the one array: calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
 // it and give wrong results.  Calls in one stream are ordered and safe.
 #include <math.h>
@@ -56,8 +61,13 @@ extern "C" int bfs_residual_static(const bfs_mesh *mesh, const double *beta, con
         return fail(BFS_EINVAL, "NULL argument");
     const int N = mesh->N, M = mesh->M;
     if (N < 4 || M < 3) return fail(BFS_EINVAL, "need N >= 4 and M >= 3");
-    if (!(mesh->dx > 0.0) || !(mesh->dy > 0.0)) return fail(BFS_EINVAL, "dx and dy must be positive");
+    // before any int arithmetic on the sizes: the same node limit as bfs_setup
+    if ((size_t)N * (size_t)M > ((size_t)1 << 26)) return fail(BFS_EINVAL, "mesh too large");
+    if (!(mesh->dx > 0.0) || !(mesh->dy > 0.0) || !isfinite(mesh->dx) || !isfinite(mesh->dy) ||
+        !isfinite(mesh->x1) || !isfinite(mesh->y1))
+        return fail(BFS_EINVAL, "dx and dy must be positive and finite, x1 and y1 finite");
     if (!(F > 0.0) || !isfinite(F)) return fail(BFS_EINVAL, "F must be positive");
+    if (!isfinite(n_rad)) return fail(BFS_EINVAL, "n_rad must be finite");
     if (mesh->half_domain && mesh->y1 != 0.0) return fail(BFS_EINVAL, "half_domain requires y1 == 0");
     if (sign_I4 != 1.0 && sign_I4 != -1.0) return fail(BFS_EINVAL, "sign_I4 must be +1 or -1");
     if (precision != BFS_FP64 && precision != BFS_FP32C) return fail(BFS_EINVAL, "bad precision");

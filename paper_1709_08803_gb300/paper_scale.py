@@ -77,7 +77,10 @@ def wake_metrics(x, y, zeta, zeta_x, zeta_y, x_from: float = 15.0, x_to: float =
 
 
 def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: int = 40, log=print,
-        F: float | None = None, on_stage=None):
+        F: float | None = None, on_stage=None, refine_below: float = 1e-5, max_krylov: int = 400,
+        u0=None):
+    """Continuation in eps from the uniform stream, or from u0 (an unknown
+    vector of a converged earlier stage, host array)."""
     import torch
 
     from . import bfs
@@ -90,8 +93,9 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
         cfg = W.config_subcritical_281
     mesh, topo, F0 = cfg(eps_list[0])
     opts = bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=1e-2, max_newton=max_newton, max_krylov=400, refine_below=1e-5,
-                               precond_precision=bfs.BFS_FP32C, half_band=half_band)
+                               eta=1e-2, max_newton=max_newton, max_krylov=max_krylov,
+                               refine_below=refine_below, precond_precision=bfs.BFS_FP32C,
+                               half_band=half_band)
     ctx = bfs.Context(mesh, topo, F0, opts)
     t0 = time.perf_counter()
     ctx.precond_factor()
@@ -99,7 +103,7 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
     factor_s = time.perf_counter() - t0
     log(f"{case} 281x281 F={F0}: {ctx.n} unknowns, {ctx.pair_evals:.3e} pair evaluations per residual, "
         f"preconditioner (half band {half_band}) factored in {factor_s:.1f} s")
-    u = ctx.flat_guess()
+    u = ctx.flat_guess() if u0 is None else torch.tensor(np.asarray(u0, dtype=np.float64), device="cuda")
     stages = []
     rep = {"case": case, "mesh": "281x281", "F": F0, "half_band": half_band, "factor_s": factor_s,
            "unknowns": mesh.n_unknowns, "pair_evals_per_residual": mesh.pair_evals(), "stages": stages}
@@ -123,7 +127,7 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
         stages.append(rec)
         log(json.dumps(rec))
         if on_stage:
-            on_stage(rep, eps, nv)
+            on_stage(rep, eps, nv, u.cpu().numpy() if st["status"] == 0 else None)
         if st["status"] != 0:
             break
     ctx.close()
@@ -227,6 +231,11 @@ def main(argv=None):
     ap.add_argument("--F", type=float, default=None, help="Froude number of the supercritical case (3)")
     ap.add_argument("--half-band", type=int, default=3)
     ap.add_argument("--max-newton", type=int, default=40)
+    ap.add_argument("--max-krylov", type=int, default=400)
+    ap.add_argument("--refine-below", type=float, default=1e-5,
+                    help="|F|inf below which the Newton residuals switch to double-float")
+    ap.add_argument("--save-u", default=None, help="unknown vector of the last converged stage (.npz)")
+    ap.add_argument("--start-u", default=None, help="start from a --save-u file instead of the uniform stream")
     ap.add_argument("--out", default=None, help="report (JSON), rewritten after every stage")
     ap.add_argument("--fields", default=None, help="surface fields of every converged stage (.npz)")
     ap.add_argument("--analyse", default=None,
@@ -258,7 +267,7 @@ def main(argv=None):
         print(json.dumps(rep))
         return 0
 
-    def on_stage(rep, eps, nv):
+    def on_stage(rep, eps, nv, u):
         if a.out:
             with open(a.out, "w") as fh:
                 json.dump(rep, fh, indent=1)
@@ -266,9 +275,17 @@ def main(argv=None):
             for k in ("zeta", "zeta_x", "zeta_y"):
                 saved[f"{k}_eps{eps:g}"] = nv[k]
             np.savez_compressed(a.fields, **saved)
+        if a.save_u and u is not None:
+            np.savez_compressed(a.save_u, u=u, eps=eps, F=rep["F"], case=rep["case"])
 
+    u0 = None
+    if a.start_u:
+        d = np.load(a.start_u)
+        u0 = d["u"]
+        print(f"starting from {a.start_u} (eps = {float(d['eps']):g})", file=sys.stderr, flush=True)
     rep = run(a.case, a.eps, a.half_band, max_newton=a.max_newton,
-              log=lambda m: print(m, file=sys.stderr, flush=True), F=a.F, on_stage=on_stage)
+              log=lambda m: print(m, file=sys.stderr, flush=True), F=a.F, on_stage=on_stage,
+              refine_below=a.refine_below, max_krylov=a.max_krylov, u0=u0)
     print(json.dumps(rep))
     return 0
 

@@ -136,3 +136,26 @@ def test_tall_bump_below_the_bernoulli_bound_is_accepted(L):
     assert rc in (bfs.BFS_OK, bfs.BFS_ECUDA, bfs.BFS_ENOMEM)
     if rc == bfs.BFS_OK:
         L.bfs_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["inf_dx", "nan_x1", "nan_n_rad", "too_many_nodes", "inf_y1"])
+def test_static_residual_rejects_invalid_input_before_device_work(L, case):
+    """bfs_residual_static checks its sizes (before any int arithmetic on them)
+    and every floating-point argument on the host, like bfs_setup."""
+    m = bfs.bfs_mesh(N=23, M=9, half_domain=0, x1=-3.3, y1=-1.4, dx=0.3, dy=0.35)
+    n_rad = 0.05
+    if case == "inf_dx":
+        m.dx = float("inf")
+    elif case == "nan_x1":
+        m.x1 = float("nan")
+    elif case == "inf_y1":
+        m.y1 = float("inf")
+    elif case == "nan_n_rad":
+        n_rad = float("nan")
+    else:
+        m.N, m.M = 1 << 14, 1 << 14
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the checks come first
+    rc = L.bfs_residual_static(ctypes.byref(m), dummy, dummy, dummy, 0.8, n_rad, -1.0, dummy, dummy,
+                               bfs.BFS_FP64, None)
+    assert rc == bfs.BFS_EINVAL
+    assert L.bfs_static_last_error()

@@ -249,6 +249,63 @@ def test_banded_jtilde():
     assert J[~keep].any()
 
 
+@pytest.mark.parametrize("half", [0, 1])
+@pytest.mark.parametrize("h", [0, 1, 2])
+def test_jtilde_band_equals_dense_band(half, h):
+    """The block-stored banded J~ (for meshes whose dense J~ does not fit in
+    memory) holds exactly the band of the dense J~ of the same linear system
+    (App. A), block (l, m) being rows of slice l and columns of slice m in the
+    order they have in F and in u."""
+    mesh = W.mesh_box(13, 7, 0.4, 0.35, half=half)
+    P = O.problem(mesh, 0.8, n_rad=0.07)
+    J = O.jtilde(P, half_band=h)
+    B = O.jtilde_band(P, h)
+    NB, M = mesh.N + 1, mesh.M
+    nb = 3 * NB
+    idx = lambda l: np.array([g * NB * M + l * NB + p for g in range(3) for p in range(NB)])
+    scale = np.abs(J).max()
+    for l in range(M):
+        for m in range(max(0, l - h), min(M, l + h + 1)):
+            ref = J[np.ix_(idx(l), idx(m))]
+            assert np.abs(B[l, m - l + h] - ref).max() <= 1e-12 * scale, (l, m)
+    # and nothing of the dense band is missing from the blocks
+    assert sum(np.abs(B[l, m - l + h]).sum() for l in range(M) for m in range(max(0, l - h), min(M, l + h + 1))) \
+        == pytest.approx(np.abs(J).sum(), rel=1e-12)
+    with pytest.raises(ValueError):
+        O.jtilde_band(O.problem(mesh, 0.8, tau=0.01), h)
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_band_lu_solves_the_banded_system(half):
+    """The block LU of App. A (partial pivoting inside the diagonal blocks)
+    solves the banded J~ as a dense library solve does."""
+    mesh = W.mesh_box(15, 9, 0.4, 0.4, half=half)
+    P = O.problem(mesh, 0.9)
+    h = 2
+    J = O.jtilde(P, half_band=h)
+    B = O.jtilde_band(P, h)
+    piv = O.band_factor(P, B)
+    r = np.random.default_rng(21).standard_normal(mesh.n_unknowns)
+    z = O.band_solve(P, B, piv, r)
+    ref = np.linalg.solve(J, r)
+    assert np.abs(z - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_jfnk_with_banded_block_lu_reaches_the_dense_root():
+    """Sec. 3.2 with the block-stored banded preconditioner (the form the
+    oracle takes on paper-scale meshes) converges to the root the dense-LU
+    preconditioner finds."""
+    mesh, topo, F = W.config_small_half()
+    P = O.problem(mesh, F)
+    u0 = W.flat_guess(mesh)
+    ud, sd = O.jfnk(P, topo, u0, half_band=1, tol=1e-11)
+    ub, sb = O.jfnk(P, topo, u0, half_band=1, tol=1e-11, banded=True)
+    assert sd["status"] == 0 and sb["status"] == 0
+    assert np.abs(O.nodal_values(P, ub)["zeta"] - O.nodal_values(P, ud)["zeta"]).max() < 1e-10
+    # the preconditioners are the same matrix, so GMRES takes the same path
+    assert abs(sb["krylov_its"] - sd["krylov_its"]) <= 2
+
+
 def _golden_appB():
     rows = []
     with open(os.path.join(GOLDEN, "appB_linear_jacobian.txt")) as fh:
