@@ -33,8 +33,8 @@ METRIC = "JFNK solve time & residual pair-evals/s at 181x61, mixed+learned vs pl
 UNIT = "pair-evals/s"
 # algorithmic work of the FP32C pair kernel per (target half point, source node)
 # index pair: 46 FP32 ALU instructions + 5 MUFU rsqrt = 51 issue slots
-INSTR_PER_INDEX_PAIR = 51  # 46 FP32 operations + 5 reciprocal square roots per index pair
-FP32_OPS_PER_INDEX_PAIR = 46
+INSTR_PER_INDEX_PAIR = 50  # 45 FP32 operations + 5 reciprocal square roots per index pair
+FP32_OPS_PER_INDEX_PAIR = 45
 MUFU_PER_INDEX_PAIR = 5  # reciprocal square roots per (target, source) index pair
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP32C pair-kernel launch at
 # 181x61 from an ncu capture of the current kernel; None until captured
@@ -608,7 +608,7 @@ def main():
     alu = measure_alu_peaks()
     avg32 = ms32 / max(n32, 1)
     pairs_per_s = n_index_pairs / (avg32 / 1e3) if n32 else None
-    # the binding pipe: the 46 FP32 operations of an index pair on the FMA pipe
+    # the binding pipe: the 45 FP32 operations of an index pair on the FMA pipe
     # (128 lane-ops/clk/SM whether packed or not; packing only halves the issue
     # slots), ahead of its 5 reciprocal square roots on the special-function
     # unit (16 lanes/clk/SM)

@@ -388,16 +388,102 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmBatch gb, int n, double alpha
     }
 }
 
+// The same GEMM in double-float arithmetic on the FP32 pipes (about 40 T
+// lane-ops/s on GB300 against 0.6 T for FP64 FMA).  Each FP64 operand is split
+// as its tile is staged into an FP32 pair hi = fl(x), lo = fl(x - hi) (48
+// significant bits).  A product is hi*hi exactly -- the FMA returns the
+// rounding error of the rounded product (Dekker) -- plus the cross terms
+// hi*lo + lo*hi in FP32; lo*lo, below 2^-48 of it, is dropped.  The running
+// sum is an unevaluated pair: Knuth's two-sum on the high parts, the errors and
+// cross terms added into the low part.  Each step is exact to about 2^-46, so
+// the product is FP64-grade for a preconditioner (relative error of order
+// K 2^-48).  The explicit _rn intrinsics keep the compiler from contracting
+// the product into the two-sum, which would break its exactness.
+__global__ void __launch_bounds__(256) k_dfgemm(GemmBatch gb, int n, double alpha, double beta)
+{
+    __shared__ float Ah[TK][TM + 1], Al[TK][TM + 1];
+    __shared__ float Bh[TK][TN + 1], Bl[TK][TN + 1];
+    const double *A = gb.A[blockIdx.z], *B = gb.B[blockIdx.z];
+    double *C = gb.C[blockIdx.z];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) { hi[i][j] = 0.f; lo[i][j] = 0.f; }
+    for (int k0 = 0; k0 < n; k0 += TK) {
+        for (int e = threadIdx.x; e < TM * TK; e += 256) {
+            int r = e / TK, kk = e % TK;
+            int gr = row0 + r, gk = k0 + kk;
+            const double v = (gr < n && gk < n) ? A[(size_t)gr * n + gk] : 0.0;
+            const float h = (float)v;
+            Ah[kk][r] = h;
+            Al[kk][r] = (float)(v - (double)h);
+        }
+        for (int e = threadIdx.x; e < TK * TN; e += 256) {
+            int kk = e / TN, cc = e % TN;
+            int gk = k0 + kk, gc = col0 + cc;
+            const double v = (gk < n && gc < n) ? B[(size_t)gk * n + gc] : 0.0;
+            const float h = (float)v;
+            Bh[kk][cc] = h;
+            Bl[kk][cc] = (float)(v - (double)h);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < TK; kk++) {
+            float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) { ah[i] = Ah[kk][ty * 4 + i]; al[i] = Al[kk][ty * 4 + i]; }
+#pragma unroll
+            for (int j = 0; j < 4; j++) { bh[j] = Bh[kk][tx * 4 + j]; bl[j] = Bl[kk][tx * 4 + j]; }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float p = __fmul_rn(ah[i], bh[j]);
+                    float e = fmaf(ah[i], bh[j], -p);
+                    e = fmaf(ah[i], bl[j], e);
+                    e = fmaf(al[i], bh[j], e);
+                    const float sm = __fadd_rn(hi[i][j], p);
+                    const float bp = __fsub_rn(sm, hi[i][j]);
+                    const float err = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(sm, bp)), __fsub_rn(p, bp));
+                    hi[i][j] = sm;
+                    lo[i][j] = __fadd_rn(lo[i][j], __fadd_rn(err, e));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int gr = row0 + ty * 4 + i;
+        if (gr >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int gc = col0 + tx * 4 + j;
+            if (gc >= n) continue;
+            double *cp = C + (size_t)gr * n + gc;
+            const double v = (double)hi[i][j] + (double)lo[i][j];
+            *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
+        }
+    }
+}
+
+// Batched block products of the factorisation: FP64 when the sweeps are FP64,
+// double-float when they sweep FP32 copies of the factors (whose own rounding
+// is 2^-24, so the factors' 2^-46 is far below what the sweeps see).
 static int gemm_batch(bfs_ctx *c, std::vector<const double *> &A, std::vector<const double *> &B,
                       std::vector<double *> &C, double alpha, double beta, cudaStream_t s)
 {
     const int nb = c->nb;
+    const bool df = c->opt.precond_precision == BFS_FP32C && c->opt.surface_tension == 0.0;
     for (size_t o = 0; o < A.size(); o += GB_MAX) {
         GemmBatch gb;
         int cnt = (int)std::min<size_t>(GB_MAX, A.size() - o);
         for (int i = 0; i < cnt; i++) { gb.A[i] = A[o + i]; gb.B[i] = B[o + i]; gb.C[i] = C[o + i]; }
         dim3 grid((nb + TN - 1) / TN, (nb + TM - 1) / TM, cnt);
-        k_dgemm<<<grid, 256, 0, s>>>(gb, nb, alpha, beta);
+        if (df) k_dfgemm<<<grid, 256, 0, s>>>(gb, nb, alpha, beta);
+        else k_dgemm<<<grid, 256, 0, s>>>(gb, nb, alpha, beta);
         c->launches++;
     }
     BFS_CUDA_TRY(c, cudaGetLastError());

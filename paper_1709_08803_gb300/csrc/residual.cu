@@ -296,9 +296,12 @@ __device__ __forceinline__ void pair_tile(const R *__restrict__ src, int per_spl
 
 // ---------------------------------------------------------------------------
 // FP32C all-pairs with the packed FP32x2 arithmetic of sm_100-class GPUs: one
-// instruction applies the same operation to two sources, so the 46 FP32
+// instruction applies the same operation to two sources, so the 45 FP32
 // operations of an index pair take 23 issue slots (the five reciprocal square
-// roots stay scalar on the special-function unit).  Sources are staged in
+// roots stay scalar on the special-function unit); the FMA pipe still spends
+// one lane-cycle per operation, and it is the kernel's limit.  The quadratic
+// form of S2 is taken as s^2 + t^2 + (zeta_x* s + zeta_y* t)^2 (three
+// operations on the shared s^2 + t^2 instead of four).  Sources are staged in
 // shared memory as interleaved pairs (value v of sources 2i and 2i+1 side by
 // side, one 64-bit word), the target values are broadcast into both halves
 // once per tile, and the offsets are taken target minus source so that no
@@ -353,7 +356,7 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
     static_assert(CH % 2 == 0, "sources are taken in pairs");
     const float *sb = src + (size_t)split * per_split * REC;
     // target values broadcast into both halves; -f* for the top double layer
-    f2 TX[TPT], TY[TPT], TZ[TPT], TB[TPT], NTF[TPT], TG[TPT], CA[TPT], CB[TPT], CC[TPT], CTB[TPT], CBT[TPT];
+    f2 TX[TPT], TY[TPT], TZ[TPT], TB[TPT], NTF[TPT], TG[TPT], ZX[TPT], ZY[TPT], CTB[TPT], CBT[TPT];
     int tid[TPT];
 #pragma unroll
     for (int p = 0; p < TPT; p++) {
@@ -363,7 +366,7 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
         TX[p] = f2_pack(tr[0], tr[0]); TY[p] = f2_pack(tr[1], tr[1]);
         TZ[p] = f2_pack(tr[2], tr[2]); TB[p] = f2_pack(tr[3], tr[3]);
         NTF[p] = f2_pack(-tr[6], -tr[6]); TG[p] = f2_pack(tr[7], tr[7]);
-        CA[p] = f2_pack(tr[8], tr[8]); CB[p] = f2_pack(tr[9], tr[9]); CC[p] = f2_pack(tr[10], tr[10]);
+        ZX[p] = f2_pack(tr[4], tr[4]); ZY[p] = f2_pack(tr[5], tr[5]);
         CTB[p] = f2_pack(tr[11], tr[11]); CBT[p] = f2_pack(tr[12], tr[12]);
     }
     float hi[TPT][NACC], lo[TPT][NACC];
@@ -403,8 +406,7 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
 #pragma unroll
             for (int p = 0; p < TPT; p++) {
                 const f2 sx = f2_sub(TX[p], xs), sy = f2_sub(TY[p], ys);  // target minus source
-                const f2 syy = f2_mul(sy, sy);
-                const f2 rho2 = f2_fma(sx, sx, syy);
+                const f2 rho2 = f2_fma(sx, sx, f2_mul(sy, sy));
                 // top target, top source: w (f - f*) K1 + w zeta_x K2, and w S2
                 {
                     const f2 d = f2_sub(zs, TZ[p]);
@@ -414,8 +416,9 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
                     const f2 dens = f2_fma(NTF[p], w1, w1f);
                     L[p][0] = f2_fma(f2_mul(dens, num), ri3, L[p][0]);
                     L[p][1] = f2_fma(w2zx, ri, L[p][1]);
-                    const f2 qf = f2_fma(sx, f2_fma(CA[p], sx, f2_mul(CB[p], sy)), f2_mul(CC[p], syy));
-                    L[p][2] = f2_fma(w2, f2_rsq(qf), L[p][2]);
+                    // A s^2 + B s t + C t^2 = s^2 + t^2 + (zeta_x* s + zeta_y* t)^2
+                    const f2 mq = f2_fma(ZX[p], sx, f2_mul(ZY[p], sy));
+                    L[p][2] = f2_fma(w2, f2_rsq(f2_fma(mq, mq, rho2)), L[p][2]);
                 }
                 // top target, bottom source: -w g K1(beta) + w sigma beta_x K2(beta)
                 {
