@@ -41,7 +41,7 @@ MUFU_PER_INDEX_PAIR = 5  # reciprocal square roots per (target, source) index pa
 PAIRS_TRAFFIC = None
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP32 sweep launch at
 # 181x61 from an ncu capture of the current kernel; None until captured
-APPLY_TRAFFIC = None
+APPLY_TRAFFIC = 500.9e6  # profiles/k_apply_sweep_181x61.md
 
 
 def _pc_prec(args):
@@ -309,19 +309,16 @@ def run_apply(args):
     return 0
 
 
-def run_batch(args):
+def batch_summary(args, steps: int, warmup: int) -> dict:
     """Batched sweep: args.batch instances (F ~ U[0.5, 1.4], 1-3 Gaussians or a
     ridge, meshes 61x21 ... 241x81) solved in lockstep; one step = one batched
     solve from the uniform-stream guesses.  Preconditioners are factored and
     the persistent kernel's tile shape is tuned before the timed steps."""
     import torch
 
-    import __graft_entry__
     from paper_1709_08803_gb300 import bfs
     from paper_1709_08803_gb300 import workloads as W
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    __graft_entry__.build()
     meshes, topos, Fs = W.config_batch(seed=3, B=args.batch)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
                                eta=args.eta, max_newton=30, max_krylov=80, time_budget_s=60.0,
@@ -343,15 +340,13 @@ def run_batch(args):
     b.solve(us)
     torch.cuda.synchronize()
     first_s = time.perf_counter() - t0
-    for _ in range(max(0, args.warmup - 1)):
+    for _ in range(max(0, warmup - 1)):
         for u, v in zip(us, us0):
             u.copy_(v)
         b.solve(us)
     torch.cuda.synchronize()
     times, evals, last = [], 0.0, None
-    sampler = ClockSampler(0)
-    sampler.start()
-    for _ in range(args.steps):
+    for _ in range(steps):
         for u, v in zip(us, us0):
             u.copy_(v)
         torch.cuda.synchronize()
@@ -364,26 +359,38 @@ def run_batch(args):
         last = st
         pe = [m.pair_evals() for m in meshes]
         evals += sum(p * (s["residual_evals_fp64"] + s["residual_evals_fp32"]) for p, s in zip(pe, st))
-    clocks = sampler.stop()
     total_s = sum(times) / 1e3
     conv = [s["status"] == 0 for s in last]
-    print(json.dumps({
-        "mode": "batch", "metric": "batched sweep: pair-evals/s and solves/s", "unit": UNIT,
-        "value": evals / total_s, "instances": len(meshes), "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_s * 1e3 / args.steps, "solves_per_s": len(meshes) * args.steps / total_s,
-        "converged": int(sum(conv)),
-        "failed": [{"i": i, "F": Fs[i], "N": meshes[i].N, "status": last[i]["status"],
-                    "fnorm_inf": last[i]["fnorm_inf"]} for i in range(len(meshes)) if not conv[i]],
-        "newton_its_max": max(s["newton_its"] for s in last),
-        "krylov_its_max": max(s["krylov_its"] for s in last),
-        "pair_evals_per_batched_residual": b.pair_evals,
-        "batched_fp32c_residual_ms": tuned_ms, "tuning": tune,
-        "setup_s": setup_s, "autotune_s": tune_s, "first_solve_incl_factor_s": first_s,
-        "config": {"workload": "64 instances: F~U[0.5,1.4], 1-3 Gaussians or a ridge, meshes 61x21..241x81, "
-                               "dx=dy=0.3; mixed lockstep JFNK to |F|inf<=1e-8",
-                   "l2": "working set > L2 (preconditioners); sources of all instances fit in L2"},
-        "clocks": clocks}))
+    pair_evals_batched = b.pair_evals
     b.close()
+    return {"metric": "batched sweep: pair-evals/s and solves/s", "unit": UNIT,
+            "value": evals / total_s, "instances": len(meshes), "steps": steps, "warmup": warmup,
+            "ms_per_step": total_s * 1e3 / steps, "solves_per_s": len(meshes) * steps / total_s,
+            "converged": int(sum(conv)),
+            "failed": [{"i": i, "F": Fs[i], "N": meshes[i].N, "status": last[i]["status"],
+                        "fnorm_inf": last[i]["fnorm_inf"]} for i in range(len(meshes)) if not conv[i]],
+            "newton_its_max": max(s["newton_its"] for s in last),
+            "krylov_its_max": max(s["krylov_its"] for s in last),
+            "pair_evals_per_batched_residual": pair_evals_batched,
+            "batched_fp32c_residual_ms": tuned_ms, "tuning": tune,
+            "setup_s": setup_s, "autotune_s": tune_s, "first_solve_incl_factor_s": first_s,
+            "config": {"workload": f"{len(meshes)} instances: F~U[0.5,1.4], 1-3 Gaussians or a ridge, "
+                                   "meshes 61x21..241x81, dx=dy=0.3; mixed lockstep JFNK to |F|inf<=1e-8",
+                       "l2": "working set > L2 (preconditioners); sources of all instances fit in L2"}}
+
+
+def run_batch(args):
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    __graft_entry__.build()
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = batch_summary(args, args.steps, args.warmup)
+    res["clocks"] = sampler.stop()
+    print(json.dumps(dict({"mode": "batch"}, **res)))
     return 0
 
 
@@ -404,6 +411,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-large", action="store_true", help="skip the 361x121 residual throughput key")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep key")
     ap.add_argument("--no-learned", action="store_true",
                     help="time the solve from the uniform stream even when trained weights exist")
     ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch", "apply"],
@@ -473,14 +481,11 @@ def main():
         return ctx.solve(u)
 
     def solve_learned():
-        net.guess(ctx, xfeat, u)
-        st = ctx.solve(u, raise_on_error=False)
-        if st["status"] != 0:  # accepted only through Newton; else the uniform stream
-            fallbacks[0] += 1
-            st2 = solve_flat()
-            for k in ("newton_its", "krylov_its", "residual_evals_fp64", "residual_evals_fp32"):
-                st2[k] += st[k]
-            st = st2
+        # bfs_cno_solve: the guess, Newton from it, the uniform stream if that fails
+        st = net.solve(ctx, xfeat, u)
+        fallbacks[0] += int(st["fallback"])
+        if st["status"] != 0:
+            raise RuntimeError(f"solve failed: {st}")
         return st
 
     one_solve = solve_learned if net is not None else solve_flat
@@ -558,17 +563,17 @@ def main():
         # guess network, the solve, the solution read back
         feat_host = torch.tensor(S.features(mesh, topo, F)[None]).pin_memory()
         out_host = torch.empty(ctx.n, dtype=torch.float64).pin_memory()
+        feat_np, out_np = feat_host.numpy(), out_host.numpy()
         h2d, d2h = feat_host.numel() * 4, 8 * ctx.n
         for i in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            xfeat.copy_(feat_host, non_blocking=True)
-            st = solve_learned()
-            out_host.copy_(u, non_blocking=True)
+            st = net.solve_host(ctx, feat_np, out_np)  # bfs_cno_solve_host: copies in and out inside
+            fallbacks[0] += int(st["fallback"])
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
             e2e_evals += st["residual_evals_fp64"] + st["residual_evals_fp32"]
-        e2e_entry = "features (pinned host) -> bfs_cno_guess -> bfs_solve -> u (pinned host)"
+        e2e_entry = "bfs_cno_solve_host: features (pinned host) -> guess network -> bfs_solve (uniform stream as fallback) -> u (pinned host)"
     else:
         u_host = np.ascontiguousarray(u0.cpu().numpy())
         pin = torch.empty(ctx.n, dtype=torch.float64).pin_memory()
@@ -688,6 +693,12 @@ def main():
             large["oracle_cores"] = cores5
             large["oracle_sample"] = f"one full FP64 oracle residual ({dt5:.2f} s)"
 
+    # ---- the batched sweep (64 uneven instances, lockstep): one solve after a
+    # warm-up that factors the preconditioners, outside the timed region
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = batch_summary(args, steps=1, warmup=1)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -722,6 +733,7 @@ def main():
                 "roofline": roofline, "roofline_pairs": roofline_pairs, "roofline_apply": roofline_apply,
                 "cpu_baseline": cpu,
                 "large_361x121": large,
+                "batch_64": batch,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "entry": e2e_entry,
                         "ms_per_step": 1e3 * sum(e2e_times) / len(e2e_times), "steps": len(e2e_times)},

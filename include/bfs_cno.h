@@ -90,6 +90,25 @@ int bfs_cno_read_loss(bfs_cno *net, float *loss_host, void *stream);
    N x M nodes. */
 int bfs_cno_guess(bfs_cno *net, bfs_ctx *ctx, const float *x, double *u, void *stream);
 
+/* The learned start of a solve: u = the network's guess from the features x
+   (device, as for bfs_cno_guess), then bfs_solve from it; the guess is
+   accepted only through Newton to the solver's tolerance, and when that solve
+   fails (BFS_ENOCONV, BFS_ELINESEARCH, BFS_EBREAKDOWN, BFS_ENAN, BFS_ETIMEOUT)
+   u is reset to the uniform stream and solved again -- the method without the
+   network.  u: device vector of bfs_n_unknowns(ctx).  st (optional) receives
+   the counts and time of both solves summed, *used_fallback (optional) 1 if
+   the uniform stream was needed.  Returns the final solve's status.
+   Synchronous. */
+int bfs_cno_solve(bfs_cno *net, bfs_ctx *ctx, const float *x, double *u, bfs_stats *st, int *used_fallback,
+                  void *stream);
+
+/* bfs_cno_solve on HOST buffers: the features x_host (M*N*4 floats, as for
+   bfs_cno_guess) are copied to the device, the solution copied back into
+   u_host (bfs_n_unknowns(ctx) doubles); both copies inside the call.
+   Synchronous. */
+int bfs_cno_solve_host(bfs_cno *net, bfs_ctx *ctx, const float *x_host, double *u_host, bfs_stats *st,
+                       int *used_fallback, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -206,6 +206,7 @@ int bfs_batch_setup(int B, const bfs_mesh *meshes, const bfs_topo *topos, const 
     std::vector<bfs::BatchInst> inst(B);
     for (int i = 0; i < B; i++) {
         inst[i].src = b->c[i]->d_src32;
+        inst[i].flag = b->c[i]->d_flag;
         inst[i].tgt = b->c[i]->d_tgt32;
         inst[i].part = b->c[i]->d_part;
         inst[i].Nt = b->c[i]->Nt;

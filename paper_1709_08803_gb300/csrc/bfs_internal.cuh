@@ -42,6 +42,7 @@ struct BatchInst {
     const float *src;
     const float *tgt;
     double *part;
+    int *flag;  // the instance's status word (bit 2: a wait timed out)
     int Nt, per_split;
 };
 
@@ -148,7 +149,9 @@ struct bfs_ctx {
     int gm_warm, gm_disabled;
     int ldp32;                   // padded row length of d_pc32
     int flow_checked;
-    double *d_gj;      // 2 * nb * 2nb  Gauss-Jordan ping-pong
+    double *d_gj;      // Gauss-Jordan work matrices and GEMM scratch
+    void *d_gjscr;     // dataflow Gauss-Jordan: candidate slots, perm / pinv
+    double *d_gjdata;  // dataflow Gauss-Jordan: candidate rows
     double *d_rowsum5; // Nt
     int *d_pivflag;
     double *d_perm_a, *d_perm_b;  // n each

@@ -327,6 +327,7 @@ struct bfs_cno {
     __nv_bfloat16 *gz;           // BF16 gradient w.r.t. pre-activations
     float *loss;
     float *scale;                // output scales (3)
+    float *xin;                  // features of one image copied from the host (bfs_cno_solve_host)
     int step;
     std::string err;
 };
@@ -425,6 +426,7 @@ void bfs_cno_destroy(bfs_cno *n)
     }
     cudaFree(n->ga);
     cudaFree(n->gz);  // loss and scale live inside the parameter allocation
+    cudaFree(n->xin);
     delete n;
 }
 
@@ -453,6 +455,7 @@ int bfs_cno_create(int H, int W, int Bmax, bfs_cno **out)
             ok = ok && cudaMalloc(&n->act[l], sizeof(__nv_bfloat16) * P * CIN[l]) == cudaSuccess;
         }
         ok = ok && cudaMalloc(&n->ga, sizeof(float) * P * 32) == cudaSuccess;
+        ok = ok && cudaMalloc(&n->xin, sizeof(float) * (size_t)H * W * 4) == cudaSuccess;
         ok = ok && cudaMalloc(&n->gz, sizeof(__nv_bfloat16) * P * 32) == cudaSuccess;
     }
     if (!ok || cudaMemset(n->p, 0, sizeof(float) * (4 * (size_t)n->np + 4)) != cudaSuccess) {
@@ -555,6 +558,56 @@ int bfs_cno_guess(bfs_cno *n, bfs_ctx *c, const float *x, double *u, void *strea
     const int tot = 3 * (c->N + 1) * c->M;
     k_fields_to_u<<<(tot + 255) / 256, 256, 0, s>>>(n->z[NL - 1], n->scale, u, c->N, c->M, c->dx, c->x1);
     return cudaGetLastError() == cudaSuccess ? BFS_OK : ferr(n, BFS_ECUDA, "guess launch failed");
+}
+
+int bfs_cno_solve(bfs_cno *n, bfs_ctx *c, const float *x, double *u, bfs_stats *st, int *used_fallback,
+                  void *stream)
+{
+    if (!n || !c || !x || !u) return ferr(n, BFS_EINVAL, "NULL argument");
+    if (used_fallback) *used_fallback = 0;
+    int rc = bfs_cno_guess(n, c, x, u, stream);
+    if (rc) return rc;
+    bfs_stats s1{};
+    rc = bfs_solve(c, u, &s1, stream);
+    if (st) *st = s1;
+    // accepted only through Newton: a guess from which the solve fails gives way
+    // to the method without the network, the uniform stream
+    if (rc == BFS_OK || !(rc == BFS_ENOCONV || rc == BFS_ELINESEARCH || rc == BFS_EBREAKDOWN ||
+                          rc == BFS_ENAN || rc == BFS_ETIMEOUT))
+        return rc;
+    if (used_fallback) *used_fallback = 1;
+    bfs_stats s2{};
+    if ((rc = bfs_flat_guess(c, u, stream))) return rc;
+    rc = bfs_solve(c, u, &s2, stream);
+    if (st) {
+        s2.newton_its += s1.newton_its;
+        s2.krylov_its += s1.krylov_its;
+        s2.residual_evals_fp64 += s1.residual_evals_fp64;
+        s2.residual_evals_fp32 += s1.residual_evals_fp32;
+        s2.precond_applies += s1.precond_applies;
+        s2.seconds += s1.seconds;
+        *st = s2;
+    }
+    return rc;
+}
+
+int bfs_cno_solve_host(bfs_cno *n, bfs_ctx *c, const float *x_host, double *u_host, bfs_stats *st,
+                       int *used_fallback, void *stream)
+{
+    if (!n || !c || !x_host || !u_host) return ferr(n, BFS_EINVAL, "NULL argument");
+    if (c->M != n->H || c->N != n->W) return ferr(n, BFS_EINVAL, "mesh does not match the network grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = bfs::alloc_solver(c);
+    if (rc) return ferr(n, rc, c->err);
+    double *u = c->d_uio;  // the context's own device copy of the iterate
+    if (cudaMemcpyAsync(n->xin, x_host, sizeof(float) * (size_t)n->H * n->W * 4, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return ferr(n, BFS_ECUDA, "upload of the features failed");
+    rc = bfs_cno_solve(n, c, n->xin, u, st, used_fallback, stream);
+    if (cudaMemcpyAsync(u_host, u, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return rc ? rc : ferr(n, BFS_ECUDA, "download of u failed");
+    return rc;
 }
 
 }  // extern "C"

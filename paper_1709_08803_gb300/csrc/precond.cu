@@ -194,7 +194,7 @@ __global__ void k_form_sparse(PcArgs a, double *pc)
 // block (l, l') when it lies in the band.  One thread per F1 row.
 __global__ void k_form_tension(PcArgs a, double *pc)
 {
-    const int N = a.N, M = a.M, NB = a.N + 1, nb = a.nb, h = a.h;
+    const int N = a.N, M = a.M, nb = a.nb, h = a.h;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M * (N - 1)) return;
     const int l = e / (N - 1), k = e % (N - 1) + 1;  // k 1-based
@@ -295,6 +295,217 @@ __global__ void __launch_bounds__(256) k_gj_coop(GjSet set, int nb, int *pivflag
         const double *t = Xi;
         Xi = Xo;
         Xo = const_cast<double *>(t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// In-place Gauss-Jordan inversion with partial pivoting, rows resident in
+// shared memory, no grid barrier.  CTA group g of a launch inverts matrix g
+// (one or two matrices, n x n row-major, FP64); CTA b of the group keeps a
+// contiguous run of rows in shared memory for the whole inversion.  Pivoting
+// is implicit (rows are never moved): the pivot of column k is the unused row
+// with the largest |S[i][k]|, and the update, applied to every row i != p,
+//   S[p][j] /= a (j != k), S[p][k] = 1/a;  S[i][j] -= S[i][k] S[p][j] / a (j != k),
+//   S[i][k] = -S[i][k] / a          (a = S[p][k])
+// stores in column k the column p of the growing inverse transformation, so
+// that at the end A^-1[k][j] = S[perm[k]][pinv[j]] (perm[k]: the pivot row of
+// column k) -- the gather k_gj_unperm undoes the permutation.
+//
+// Instead of a grid barrier per column, every CTA publishes, for the next
+// column, its best candidate (|value| and row, then a tag word released after
+// the candidate row's data) in a slot of its own; the CTAs of the group poll
+// the tags, agree on the largest candidate (ties: the lowest row) and read
+// its row from the winner's slot.  Slots alternate between two parities, so a
+// CTA may publish column k+1 while slower ones still read column k.  The
+// launch is cooperative (all CTAs resident); each poll is bounded, after which
+// bit 2 of *flag is raised and the CTA returns.
+// ---------------------------------------------------------------------------
+constexpr int GJR_TPB = 256;
+constexpr int GJR_MAXR = 16;  // rows per CTA
+
+struct GjRowsArgs {
+    double *S0, *S1;            // the matrices in; the in-place result out
+    int n, nmat, G;             // G: CTAs per matrix
+    unsigned long long *slot;   // [2 parities][nmat G][2]: |value| bits, (row << 32) | tag
+    double *data;               // [2 parities][nmat G][n]: candidate rows
+    int *perm;                  // [nmat][2 n]: perm, then pinv
+    int *pivflag, *flag;
+    unsigned int spin;
+};
+
+__device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_rel_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(GJR_TPB) k_gj_rows(GjRowsArgs a)
+{
+    extern __shared__ double gsm[];  // nr rows of n, then the scaled pivot row (n)
+    __shared__ double rv[GJR_TPB / 32];
+    __shared__ int ri[GJR_TPB / 32], rrow[GJR_TPB / 32];
+    __shared__ double fcol[GJR_MAXR];
+    __shared__ unsigned char used[GJR_MAXR];
+    __shared__ double cand_v;
+    __shared__ int cand_sh, win_sh, ok_sh, prow_sh;
+    const int n = a.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mat = blockIdx.x / a.G, lb = blockIdx.x - mat * a.G;
+    if (mat >= a.nmat) return;
+    const int Geff = min(a.G, n);
+    if (lb >= Geff) return;  // no rows here
+    const int base = n / Geff, extra = n % Geff;
+    const int nr = base + (lb < extra ? 1 : 0), r0 = lb * base + min(lb, extra);
+    const int NS = a.nmat * a.G, me = mat * a.G + lb, s0 = mat * a.G;
+    double *S = gsm, *pr = gsm + (size_t)nr * n;
+    double *Mg = mat ? a.S1 : a.S0;
+    for (int e = tid; e < nr * n; e += GJR_TPB) S[e] = Mg[(size_t)r0 * n + e];
+    if (tid < GJR_MAXR) used[tid] = 0;
+    __syncthreads();
+
+    // candidate of this CTA for column k into the slots of parity par
+    auto publish = [&](int k, int par) {
+        if (warp == 0) {
+            double v = -1.0;
+            int i = -1;
+            for (int r = lane; r < nr; r += 32)
+                if (!used[r]) {
+                    const double x = fabs(S[(size_t)r * n + k]);
+                    if (x > v || i < 0) { v = x; i = r; }
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, v, o);
+                const int oi = __shfl_down_sync(0xffffffffu, i, o);
+                if (oi >= 0 && (i < 0 || ov > v || (ov == v && oi < i))) { v = ov; i = oi; }
+            }
+            if (lane == 0) { cand_sh = i; cand_v = v; }
+        }
+        __syncthreads();
+        const int ci = cand_sh;
+        double *d = a.data + ((size_t)par * NS + me) * n;
+        if (ci >= 0)
+            for (int j = tid; j < n; j += GJR_TPB) __stcg(d + j, S[(size_t)ci * n + j]);
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long *sl = a.slot + ((size_t)par * NS + me) * 2;
+            const unsigned int row = ci >= 0 ? (unsigned int)(r0 + ci) : 0x7fffffffu;
+            __threadfence();
+            __stcg(reinterpret_cast<double *>(sl), ci >= 0 ? cand_v : -1.0);
+            st_rel_u64(sl + 1, ((unsigned long long)row << 32) | (unsigned int)(k + 1));
+        }
+    };
+
+    publish(0, 0);
+    for (int k = 0; k < n; k++) {
+        const int par = k & 1;
+        // the candidates of every CTA of the group: thread t polls CTA t's slot
+        double v = -1.0;
+        int row = 0x7fffffff, who = -1;
+        bool ok = true;
+        for (int t = tid; t < Geff; t += GJR_TPB) {
+            const unsigned long long *sl = a.slot + ((size_t)par * NS + s0 + t) * 2;
+            unsigned long long w = ld_acq_u64(sl + 1);
+            unsigned int spins = 0;
+            while ((unsigned int)w != (unsigned int)(k + 1)) {
+                if (++spins > a.spin) { ok = false; break; }
+                __nanosleep(20);
+                w = ld_acq_u64(sl + 1);
+            }
+            if (!ok) break;
+            const double x = __ldcg(reinterpret_cast<const double *>(sl));
+            const int r = (int)(w >> 32);
+            if (x > v || (x == v && r < row)) { v = x; row = r; who = t; }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(a.flag, 2);
+            return;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, v, o);
+            const int orow = __shfl_down_sync(0xffffffffu, row, o), ow = __shfl_down_sync(0xffffffffu, who, o);
+            if (ov > v || (ov == v && orow < row)) { v = ov; row = orow; who = ow; }
+        }
+        if (lane == 0) { rv[warp] = v; ri[warp] = who; rrow[warp] = row; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = -1.0;
+            int w = -1, wr = 0x7fffffff;
+            for (int q = 0; q < GJR_TPB / 32; q++) {
+                if (ri[q] < 0) continue;
+                if (w < 0 || rv[q] > b || (rv[q] == b && rrow[q] < wr)) { b = rv[q]; w = ri[q]; wr = rrow[q]; }
+            }
+            win_sh = w;
+            prow_sh = wr;
+            ok_sh = (w >= 0 && b > 0.0);
+            if (!ok_sh && lb == 0) atomicOr(a.pivflag, 1);
+        }
+        __syncthreads();
+        // the winner's data: its tag was acquired by the polling thread before the
+        // barrier above, which orders these reads after it
+        const int w = win_sh, p = prow_sh;
+        const double *pd = a.data + ((size_t)par * NS + s0 + max(w, 0)) * n;
+        const double piv = __ldcg(pd + k);
+        const double inv = (ok_sh && piv != 0.0) ? 1.0 / piv : 0.0;
+        for (int j = tid; j < n; j += GJR_TPB) pr[j] = __ldcg(pd + j) * inv;
+        for (int i = tid; i < nr; i += GJR_TPB) fcol[i] = S[(size_t)i * n + k];
+        if (lb == 0 && tid == 0) a.perm[(size_t)mat * 2 * n + k] = p;
+        __syncthreads();
+        // the update of every row of this CTA
+        const int ip = (p >= r0 && p < r0 + nr) ? p - r0 : -1;
+        for (int i = 0; i < nr; i++) {
+            double *Si = S + (size_t)i * n;
+            const double f = fcol[i];
+            if (i == ip) {
+                for (int j = tid; j < n; j += GJR_TPB) Si[j] = j == k ? inv : pr[j];
+            } else {
+                for (int j = tid; j < n; j += GJR_TPB) Si[j] = j == k ? -f * inv : fma(-f, pr[j], Si[j]);
+            }
+        }
+        if (ip >= 0 && tid == 0) used[ip] = 1;
+        __syncthreads();
+        if (k + 1 < n) publish(k + 1, par ^ 1);
+    }
+    for (int e = tid; e < nr * n; e += GJR_TPB) Mg[(size_t)r0 * n + e] = S[e];
+    if (lb == 0) {  // the inverse permutation (perm is complete: this CTA recorded it)
+        __syncthreads();
+        int *pm = a.perm + (size_t)mat * 2 * n;
+        for (int k2 = tid; k2 < n; k2 += GJR_TPB) pm[n + pm[k2]] = k2;
+    }
+}
+
+// One nb x nb block into (or out of) a row-major matrix of row length ld at block (a, b).
+__global__ void k_blk_put(const double *__restrict__ D, double *__restrict__ X, int nb, int ld, int a, int b)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / nb), c = (int)(e % nb);
+        X[(size_t)(a * nb + r) * ld + b * nb + c] = D[e];
+    }
+}
+
+__global__ void k_blk_get(const double *__restrict__ X, double *__restrict__ D, int nb, int ld, int a, int b)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nb * nb;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / nb), c = (int)(e % nb);
+        D[e] = X[(size_t)(a * nb + r) * ld + b * nb + c];
+    }
+}
+
+// A^-1[k][j] = S[perm[k]][pinv[j]] into the destination (row-major, ld n).
+__global__ void k_gj_unperm(const double *__restrict__ S, const int *__restrict__ perm, double *__restrict__ D,
+                            int n)
+{
+    const int *pinv = perm + n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), j = (int)(e % n);
+        D[e] = S[(size_t)perm[k] * n + pinv[j]];
     }
 }
 
@@ -714,6 +925,10 @@ void precond_free(bfs_ctx *c)
     c->sweep_ntags = 0;
     c->pc_twist = -1;
     cudaFree(c->d_gj);
+    cudaFree(c->d_gjscr);
+    cudaFree(c->d_gjdata);
+    c->d_gjscr = nullptr;
+    c->d_gjdata = nullptr;
     cudaFree(c->d_rowsum5);
     cudaFree(c->d_pivflag);
     cudaFree(c->d_perm_a);
@@ -751,6 +966,44 @@ static int gj_invert(bfs_ctx *c, GjSet set, int n, double **res, cudaStream_t s)
     return BFS_OK;
 }
 
+// In-place inversion of one or two n x n matrices (row-major, contiguous) by
+// k_gj_rows, results gathered into dst[i] (which may be another buffer).
+// Returns 1 if the kernel's tiles do not take n (the caller falls back).
+static int gj_rows_invert(bfs_ctx *c, double *const *work, double *const *dst, int nmat, int n, cudaStream_t s)
+{
+    const int G = num_sms(c->device) / nmat;
+    const int Geff = std::min(G, n), rmax = (n + Geff - 1) / Geff;
+    const size_t smem = sizeof(double) * (size_t)(rmax + 1) * n;
+    if (rmax > GJR_MAXR || smem > 200 * 1024) return 1;
+    BFS_CUDA_TRY(c, cudaFuncSetAttribute((const void *)k_gj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024));
+    int per_sm = 0;
+    BFS_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_rows, GJR_TPB, smem));
+    if (per_sm < 1 || per_sm * num_sms(c->device) < G * nmat) return 1;
+    GjRowsArgs a;
+    a.S0 = work[0];
+    a.S1 = nmat > 1 ? work[1] : work[0];
+    a.n = n; a.nmat = nmat; a.G = G;
+    const int NS = nmat * G;
+    a.slot = reinterpret_cast<unsigned long long *>(c->d_gjscr);
+    a.perm = reinterpret_cast<int *>(a.slot + 4 * (size_t)NS);
+    a.data = c->d_gjdata;
+    a.pivflag = c->d_pivflag;
+    a.flag = c->d_flag;
+    a.spin = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 24);
+    BFS_CUDA_TRY(c, cudaMemsetAsync(a.slot, 0, sizeof(unsigned long long) * 4 * (size_t)NS, s));
+    void *args[] = {&a};
+    BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_gj_rows, dim3(G * nmat), dim3(GJR_TPB), args,
+                                                smem, s));
+    c->launches++;
+    for (int i = 0; i < nmat; i++) {
+        k_gj_unperm<<<1024, 256, 0, s>>>(work[i], a.perm + (size_t)i * 2 * n, dst[i], n);
+        c->launches++;
+    }
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
 int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
 {
     int h = half_band >= 0 ? half_band : c->opt.half_band;
@@ -774,8 +1027,16 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     // Gauss-Jordan buffers: two matrices of nb x 2nb ping-pong, or the h nb x 2 h nb
     // middle system; then h blocks of GEMM scratch
     const size_t gj_doubles = std::max<size_t>(8 * bsz, twist >= 0 ? 4 * (size_t)h * h * bsz : 0);
-    BFS_CUDA_TRY(c, cudaMalloc(&c->d_gj, sizeof(double) * (gj_doubles + bsz * (size_t)(h > 0 ? h : 1))));
+    // GEMM scratch: W and L of up to two eliminations at once (4 h blocks)
+    BFS_CUDA_TRY(c, cudaMalloc(&c->d_gj, sizeof(double) * (gj_doubles + bsz * 4 * (size_t)(h > 0 ? h : 1))));
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_rowsum5, sizeof(double) * (size_t)c->Nt));
+    {  // dataflow Gauss-Jordan: 2 parities x CTAs of slots, 2 x (perm, pinv) of the largest
+       // matrix, and 2 parities x CTAs candidate rows
+        const int G = num_sms(c->device), nmax = std::max(nb, twist >= 0 ? h * nb : nb);
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjscr, sizeof(unsigned long long) * 4 * (size_t)G +
+                                                    sizeof(int) * 4 * (size_t)nmax));
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjdata, sizeof(double) * 2 * (size_t)G * nmax));
+    }
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int) * 8));  // [0] pivot flag, [4..5] grid barrier
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_perm_a, sizeof(double) * 2 * (size_t)c->n));
     c->d_perm_b = c->d_perm_a + c->n;
@@ -800,6 +1061,16 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
     double *tmp = c->d_gj + gj_doubles;
     // D_k^-1 in place for the one or two diagonal blocks listed
     auto invert_diag = [&](const int *ks, int cnt) -> int {
+        {  // rows in shared memory, no grid barrier
+            double *work[2], *dst[2];
+            for (int i = 0; i < cnt; i++) {
+                work[i] = c->d_gj + (size_t)i * bsz;
+                dst[i] = B(ks[i], ks[i]);
+                BFS_CUDA_TRY(c, cudaMemcpyAsync(work[i], dst[i], sizeof(double) * bsz, cudaMemcpyDeviceToDevice, s));
+            }
+            const int r = gj_rows_invert(c, work, dst, cnt, nb, s);
+            if (r <= 0) return r;
+        }
         GjSet set;
         set.nmat = cnt;
         for (int i = 0; i < cnt; i++) {
@@ -820,35 +1091,60 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
         return BFS_OK;
     };
     // eliminate slice k (D_k^-1 in place) from the coupled slices lo..hi
-    auto eliminate = [&](int k, int lo, int hi) -> int {
-        if (hi < lo) return BFS_OK;
+    // eliminate slice k (D_k^-1 in place) from the coupled slices lo..hi, for one
+    // or two slices of the two chains at once:
+    //   W_kj = D_k^-1 S_kj and L_ik = S_ik D_k^-1 (one launch for every product),
+    //   S_ij -= S_ik W_kj (one launch, or one per chain where both would update
+    //   the same middle blocks), then W and L into their slots
+    struct Elim { int k, lo, hi; };
+    auto eliminate = [&](const Elim *es, int cnt) -> int {
         std::vector<const double *> A, Bm;
         std::vector<double *> C;
-        // W_kj = D_k^-1 S_kj into tmp, then back into slot (k, j)
-        for (int j = lo; j <= hi; j++) { A.push_back(B(k, k)); Bm.push_back(B(k, j)); C.push_back(tmp + (j - lo) * bsz); }
+        std::vector<std::pair<double *, double *>> back;  // (slot, scratch)
+        double *t = tmp;
+        for (int q = 0; q < cnt; q++) {
+            const Elim &e = es[q];
+            for (int j = e.lo; j <= e.hi; j++) {
+                A.push_back(B(e.k, e.k)); Bm.push_back(B(e.k, j)); C.push_back(t);
+                back.push_back({B(e.k, j), t});
+                t += bsz;
+            }
+            for (int i = e.lo; i <= e.hi; i++) {
+                A.push_back(B(i, e.k)); Bm.push_back(B(e.k, e.k)); C.push_back(t);
+                back.push_back({B(i, e.k), t});
+                t += bsz;
+            }
+        }
+        if (A.empty()) return BFS_OK;
         int r = gemm_batch(c, A, Bm, C, 1.0, 0.0, s);
         if (r) return r;
-        for (int j = lo; j <= hi; j++)
-            BFS_CUDA_TRY(c, cudaMemcpyAsync(B(k, j), tmp + (j - lo) * bsz, sizeof(double) * bsz,
-                                            cudaMemcpyDeviceToDevice, s));
-        // S_ij -= S_ik W_kj
+        // S_ij -= S_ik W_kj (S_ik still the unscaled block, W from the scratch)
+        const bool overlap = cnt == 2 && es[0].hi >= es[1].lo && es[1].hi >= es[0].lo;
         A.clear(); Bm.clear(); C.clear();
-        for (int i = lo; i <= hi; i++)
-            for (int j = lo; j <= hi; j++) { A.push_back(B(i, k)); Bm.push_back(B(k, j)); C.push_back(B(i, j)); }
-        if ((r = gemm_batch(c, A, Bm, C, -1.0, 1.0, s))) return r;
-        // S_ik D_k^-1 into slot (i, k)
-        A.clear(); Bm.clear(); C.clear();
-        for (int i = lo; i <= hi; i++) { A.push_back(B(i, k)); Bm.push_back(B(k, k)); C.push_back(tmp + (i - lo) * bsz); }
-        if ((r = gemm_batch(c, A, Bm, C, 1.0, 0.0, s))) return r;
-        for (int i = lo; i <= hi; i++)
-            BFS_CUDA_TRY(c, cudaMemcpyAsync(B(i, k), tmp + (i - lo) * bsz, sizeof(double) * bsz,
-                                            cudaMemcpyDeviceToDevice, s));
+        t = tmp;
+        for (int q = 0; q < cnt; q++) {
+            const Elim &e = es[q];
+            const int w = e.hi - e.lo + 1;
+            for (int i = e.lo; i <= e.hi; i++)
+                for (int j = e.lo; j <= e.hi; j++) {
+                    A.push_back(B(i, e.k)); Bm.push_back(t + (size_t)(j - e.lo) * bsz); C.push_back(B(i, j));
+                }
+            t += 2 * (size_t)w * bsz;
+            if (overlap && q == 0) {
+                if ((r = gemm_batch(c, A, Bm, C, -1.0, 1.0, s))) return r;
+                A.clear(); Bm.clear(); C.clear();
+            }
+        }
+        if (!A.empty() && (r = gemm_batch(c, A, Bm, C, -1.0, 1.0, s))) return r;
+        for (auto &bk : back)
+            BFS_CUDA_TRY(c, cudaMemcpyAsync(bk.first, bk.second, sizeof(double) * bsz, cudaMemcpyDeviceToDevice, s));
         return BFS_OK;
     };
     if (twist < 0) {
         for (int k = 0; k < M; k++) {
             if ((rc = invert_diag(&k, 1))) return rc;
-            if ((rc = eliminate(k, k + 1, std::min(M - 1, k + h)))) return rc;
+            const Elim e{k, k + 1, std::min(M - 1, k + h)};
+            if (e.hi >= e.lo && (rc = eliminate(&e, 1))) return rc;
         }
     } else {
         const int t0 = twist, t1 = twist + h;
@@ -858,12 +1154,33 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
             if (kt >= 0) ks[cnt++] = kt;
             if (kb >= 0) ks[cnt++] = kb;
             if ((rc = invert_diag(ks, cnt))) return rc;
-            // sequential: both chains may update the same middle-middle blocks
-            if (kt >= 0 && (rc = eliminate(kt, kt + 1, std::min(M - 1, kt + h)))) return rc;
-            if (kb >= 0 && (rc = eliminate(kb, std::max(0, kb - h), kb - 1))) return rc;
+            Elim es[2];
+            int ne = 0;
+            if (kt >= 0 && kt + 1 <= std::min(M - 1, kt + h)) es[ne++] = {kt, kt + 1, std::min(M - 1, kt + h)};
+            if (kb >= 0 && std::max(0, kb - h) <= kb - 1) es[ne++] = {kb, std::max(0, kb - h), kb - 1};
+            if (ne && (rc = eliminate(es, ne))) return rc;
         }
         // the middle system C (slices t0..t1-1, h nb square) inverted whole
         const int hn = h * nb;
+        {
+            double *work = c->d_gj, *out = c->d_gj + (size_t)hn * hn;
+            for (int ia = 0; ia < h; ia++)
+                for (int ib = 0; ib < h; ib++) {
+                    k_blk_put<<<512, 256, 0, s>>>(B(t0 + ia, t0 + ib), work, nb, hn, ia, ib);
+                    c->launches++;
+                }
+            rc = gj_rows_invert(c, &work, &out, 1, hn, s);
+            if (rc < 0) return rc;
+            if (rc == 0) {
+                for (int ia = 0; ia < h; ia++)
+                    for (int ib = 0; ib < h; ib++) {
+                        k_blk_get<<<512, 256, 0, s>>>(out, B(t0 + ia, t0 + ib), nb, hn, ia, ib);
+                        c->launches++;
+                    }
+                BFS_CUDA_TRY(c, cudaGetLastError());
+            }
+        }
+        if (rc == 1) {
         GjSet set;
         set.nmat = 1;
         set.X0[0] = c->d_gj;
@@ -883,6 +1200,7 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
                 c->launches++;
             }
         BFS_CUDA_TRY(c, cudaGetLastError());
+        }
     }
     c->pc_twist = twist;
     int flag = 0;

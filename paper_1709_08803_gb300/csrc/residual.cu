@@ -125,8 +125,10 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
         }
         if (a.w64)
             for (int k = 0; k < REC; k++) src64[(size_t)e * REC + k] = r[k];
-        if (a.w32)
-            for (int k = 0; k < REC; k++) src32[(size_t)e * REC + k] = (float)r[k];
+        if (a.w32) {  // sources in interleaved pairs for the packed FP32x2 pair kernel
+            float *d = src32 + (size_t)(e >> 1) * REC * 2 + (e & 1);
+            for (int k = 0; k < REC; k++) d[2 * k] = k == 10 ? -(float)r[k] : (float)r[k];
+        }
         return;
     }
     e -= a.Ns_cap;
@@ -348,13 +350,74 @@ __device__ __forceinline__ f2 f2_rsq(f2 x)
     return f2_pack(rsqrtf(a), rsqrtf(b));
 }
 
+// Two shared-memory chunk buffers filled by 1-D bulk copies (cp.async.bulk,
+// completion counted in bytes on an mbarrier per buffer): the copy of the
+// next chunk is in flight while the CTA works on the current one.  `seq`
+// counts the chunks this CTA has consumed (persistent CTAs run several tiles),
+// which fixes each chunk's buffer and mbarrier phase.  Waits are bounded: on
+// timeout bit 2 of *flag is raised, the CTA drains its copy and gives up the
+// tile (its partial sums are then not written).
+struct ChunkRing {
+    float *buf;                     // two buffers of `floats` floats, back to back
+    unsigned long long *bar;        // two mbarriers
+    unsigned int seq;
+    unsigned int floats;
+    __device__ __forceinline__ float *at(unsigned int q) const { return buf + (size_t)(q & 1) * floats; }
+};
+
+__device__ __forceinline__ unsigned int smem_addr(const void *p)
+{
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void chunk_ring_init(ChunkRing &r)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&r.bar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void chunk_issue(ChunkRing &r, unsigned int q, const float *src, unsigned int bytes)
+{
+    // thread 0 only; the generic-proxy reads of this buffer happened before a
+    // __syncthreads, the fence orders them before the async-proxy writes
+    const unsigned int b = smem_addr(&r.bar[q & 1]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(r.at(q))),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool chunk_wait(const ChunkRing &r, unsigned int q)
+{
+    const unsigned int b = smem_addr(&r.bar[q & 1]), parity = (q >> 1) & 1;
+    for (unsigned int i = 0; i < (1u << 22); i++) {
+        unsigned int done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <int TPB, int TPT, int CH>
 __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int per_split,
                                              const float *__restrict__ tgt, int Nt,
-                                             double *__restrict__ part, int tile, int split, float *sh)
+                                             double *__restrict__ part, int tile, int split, ChunkRing &ring,
+                                             int *flag)
 {
     static_assert(CH % 2 == 0, "sources are taken in pairs");
+    constexpr unsigned int CHUNK_BYTES = CH * REC * sizeof(float);
     const float *sb = src + (size_t)split * per_split * REC;
+    const int nch = per_split / CH;
     // target values broadcast into both halves; -f* for the top double layer
     f2 TX[TPT], TY[TPT], TZ[TPT], TB[TPT], NTF[TPT], TG[TPT], ZX[TPT], ZY[TPT], CTB[TPT], CBT[TPT];
     int tid[TPT];
@@ -375,27 +438,27 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
 #pragma unroll
         for (int q = 0; q < NACC; q++) { hi[p][q] = 0.f; lo[p][q] = 0.f; }
 
-    const f2 *sp2 = reinterpret_cast<const f2 *>(sh);
-    for (int c0 = 0; c0 < per_split; c0 += CH) {
-        __syncthreads();
-        // stage the chunk as interleaved source pairs: value v of source s at
-        // 2 ((s / 2) REC + v) + (s & 1); w g (value 10) negated
-        const float4 *g = reinterpret_cast<const float4 *>(sb + (size_t)c0 * REC);
-        for (int e = threadIdx.x; e < CH * REC / 4; e += TPB) {
-            const float4 v4 = g[e];
-            const int s = e / (REC / 4), v0 = (e - s * (REC / 4)) * 4;
-            float *d = sh + 2 * ((s >> 1) * REC + v0) + (s & 1);
-            d[0] = v4.x;
-            d[2] = v4.y;
-            d[4] = v0 + 2 == 10 ? -v4.z : v4.z;
-            d[6] = v4.w;
+    const unsigned int q0 = ring.seq;
+    if (threadIdx.x == 0) chunk_issue(ring, q0, sb, CHUNK_BYTES);
+    for (int c = 0; c < nch; c++) {
+        const unsigned int q = q0 + c;
+        // the next chunk into the other buffer (read by every thread before the
+        // __syncthreads that ended the previous chunk)
+        if (threadIdx.x == 0 && c + 1 < nch) chunk_issue(ring, q + 1, sb + (size_t)(c + 1) * CH * REC, CHUNK_BYTES);
+        if (!__syncthreads_and(chunk_wait(ring, q))) {
+            if (threadIdx.x == 0) {
+                atomicOr(flag, 2);
+                if (c + 1 < nch) chunk_wait(ring, q + 1);  // drain the copy in flight
+            }
+            ring.seq = q0 + nch;
+            return;
         }
-        __syncthreads();
+        const f2 *sp2 = reinterpret_cast<const f2 *>(ring.at(q));
         f2 L[TPT][NACC];
 #pragma unroll
         for (int p = 0; p < TPT; p++)
 #pragma unroll
-            for (int q = 0; q < NACC; q++) L[p][q].v = 0ull;
+            for (int qq = 0; qq < NACC; qq++) L[p][qq].v = 0ull;
 #pragma unroll 2
         for (int i = 0; i < CH / 2; i++) {
             const f2 *r = sp2 + i * REC;
@@ -452,12 +515,14 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
 #pragma unroll
         for (int p = 0; p < TPT; p++)
 #pragma unroll
-            for (int q = 0; q < NACC; q++) {
+            for (int qq = 0; qq < NACC; qq++) {
                 float a, b;
-                f2_unpack(L[p][q], a, b);
-                two_sum_acc(hi[p][q], lo[p][q], a + b);
+                f2_unpack(L[p][qq], a, b);
+                two_sum_acc(hi[p][qq], lo[p][qq], a + b);
             }
+        __syncthreads();  // every thread is done with this buffer before it is refilled
     }
+    ring.seq = q0 + nch;
 #pragma unroll
     for (int p = 0; p < TPT; p++) {
         if (tid[p] >= Nt) continue;
@@ -470,13 +535,18 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
 template <typename R, int TPB, int TPT, int CH, bool COMP>
 __global__ void __launch_bounds__(TPB)
 k_pairs(const R *__restrict__ src, int per_split, const R *__restrict__ tgt, int Nt,
-        double *__restrict__ part)
+        double *__restrict__ part, int *flag)
 {
-    __shared__ __align__(16) R sh[CH * REC];
-    if constexpr (sizeof(R) == 4 && COMP)
-        pair_tile_x2<TPB, TPT, CH>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, sh);
-    else
+    if constexpr (sizeof(R) == 4 && COMP) {
+        __shared__ __align__(128) float sh[2 * CH * REC];
+        __shared__ __align__(8) unsigned long long bar[2];
+        ChunkRing ring{sh, bar, 0u, (unsigned int)(CH * REC)};
+        chunk_ring_init(ring);
+        pair_tile_x2<TPB, TPT, CH>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, ring, flag);
+    } else {
+        __shared__ __align__(16) R sh[CH * REC];
         pair_tile<R, TPB, TPT, CH, COMP>(src, per_split, tgt, Nt, part, blockIdx.x, blockIdx.y, sh);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -744,10 +814,10 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
         if ((rc = pairs_df_launch(c, s))) return rc;
     } else if (precision == BFS_FP32C)
         k_pairs<float, P32_TPB, P32_TPT, P32_CH, true>
-            <<<grid, P32_TPB, 0, s>>>(c->d_src32, p.per_split, c->d_tgt32, c->Nt, c->d_part);
+            <<<grid, P32_TPB, 0, s>>>(c->d_src32, p.per_split, c->d_tgt32, c->Nt, c->d_part, c->d_flag);
     else
         k_pairs<double, P64_TPB, P64_TPT, P64_CH, false>
-            <<<grid, P64_TPB, 0, s>>>(c->d_src64, p.per_split, c->d_tgt64, c->Nt, c->d_part);
+            <<<grid, P64_TPB, 0, s>>>(c->d_src64, p.per_split, c->d_tgt64, c->Nt, c->d_part, c->d_flag);
     if (precision != BFS_DF64) c->launches++;
     if (ev1) cudaEventRecord(ev1, s);
     FinArgs fa = fin_args(c, p.splits);
@@ -779,8 +849,11 @@ __global__ void __launch_bounds__(TPB)
 k_pairs_batch(const BatchInst *__restrict__ inst, const int4 *__restrict__ items, int n_items,
               unsigned int *__restrict__ counter, const unsigned char *__restrict__ mask)
 {
-    __shared__ __align__(16) float sh[P32_CH * REC];
+    __shared__ __align__(128) float sh[2 * P32_CH * REC];
+    __shared__ __align__(8) unsigned long long bar[2];
     __shared__ int it;
+    ChunkRing ring{sh, bar, 0u, (unsigned int)(P32_CH * REC)};
+    chunk_ring_init(ring);
     while (true) {
         if (threadIdx.x == 0) it = (int)atomicAdd(counter, 1u);
         __syncthreads();
@@ -790,7 +863,7 @@ k_pairs_batch(const BatchInst *__restrict__ inst, const int4 *__restrict__ items
         const int4 item = items[w];
         if (!mask[item.x]) continue;
         const BatchInst I = inst[item.x];
-        pair_tile_x2<TPB, TPT, P32_CH>(I.src, I.per_split, I.tgt, I.Nt, I.part, item.y, item.z, sh);
+        pair_tile_x2<TPB, TPT, P32_CH>(I.src, I.per_split, I.tgt, I.Nt, I.part, item.y, item.z, ring, I.flag);
     }
 }
 

@@ -223,9 +223,82 @@ def compare_bump_pressure(eps: float = 0.285, half_band: int = 3, tol: float = 1
     return rep
 
 
+def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max_newton: int = 40):
+    """The large configuration (361 x 121, dx = dy = 0.2, F = 0.9, bump 0.3 plus
+    a cross-stream ridge; 7.6e9 pair evaluations per residual): the mixed form
+    from the uniform stream and from the guess network's output (accepted only
+    through Newton, the uniform stream as fallback), and the plain FP64 form
+    from the uniform stream.  Reports each solve's counts and time, and how far
+    the mixed solutions lie from the FP64 one."""
+    import torch
+
+    from . import bfs
+    from . import surrogate as S
+    from . import workloads as W
+
+    mesh, topo, F = W.config_large()
+    mixed = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
+                                eta=1e-2, forcing=1, max_newton=max_newton, max_krylov=400,
+                                refine_below=1e-5, precond_precision=bfs.BFS_FP32C)
+    rep = {"case": "large", "mesh": "361x121", "F": F, "unknowns": mesh.n_unknowns,
+           "pair_evals_per_residual": mesh.pair_evals(), "solves": {}}
+    ctx = bfs.Context(mesh, topo, F, mixed)
+    t0 = time.perf_counter()
+    ctx.precond_factor()
+    torch.cuda.synchronize()
+    rep["factor_s_mixed"] = time.perf_counter() - t0
+    rep["precond"] = ctx.precond_info()
+
+    def solve(c, u, name):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st = c.solve(u, raise_on_error=False)
+        torch.cuda.synchronize()
+        rec = {"status": st["status"], "newton": st["newton_its"], "krylov": st["krylov_its"],
+               "evals_fp32c": st["residual_evals_fp32"], "evals_fp64": st["residual_evals_fp64"],
+               "fnorm_inf": st["fnorm_inf"], "seconds": time.perf_counter() - t}
+        rep["solves"][name] = rec
+        log(json.dumps({name: rec}))
+        return u
+
+    u_flat = solve(ctx, ctx.flat_guess(), "mixed_uniform_stream")
+    if with_learned:
+        import os
+        if os.path.exists(S.WEIGHTS):
+            params, scale = S.load(S.WEIGHTS)
+            net = S.CNO(mesh.M, mesh.N, 1)
+            net.set_params(params, scale)
+            x = torch.tensor(S.features(mesh, topo, F)[None], device="cuda")
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            u = net.guess(ctx, x)
+            torch.cuda.synchronize()
+            guess_s = time.perf_counter() - t
+            u = solve(ctx, u, "mixed_learned")
+            rep["solves"]["mixed_learned"]["guess_s"] = guess_s
+            if rep["solves"]["mixed_learned"]["status"] != 0:  # the method without the network
+                u = solve(ctx, ctx.flat_guess(), "mixed_learned_fallback")
+            net.close()
+    z = ctx.unpack(u_flat)["zeta"]
+    rep["zeta_max"] = float(z.max())
+    ctx.close()
+    if with_plain:
+        ctx64 = bfs.Context(mesh, topo, F, bfs.default_options(tol=1e-8, forcing=1, max_newton=max_newton,
+                                                               max_krylov=400))
+        t0 = time.perf_counter()
+        ctx64.precond_factor()
+        torch.cuda.synchronize()
+        rep["factor_s_fp64"] = time.perf_counter() - t0
+        u64 = solve(ctx64, ctx64.flat_guess(), "plain_fp64")
+        z64 = ctx64.unpack(u64)["zeta"]
+        rep["max_abs_zeta_mixed_minus_fp64"] = float((z - z64).abs().max())
+        ctx64.close()
+    return rep
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="super", choices=["super", "sub", "compare"],
+    ap.add_argument("--case", default="super", choices=["super", "sub", "compare", "large"],
                     help="compare: bump vs equivalent pressure at eps = the first --eps (Sec. 6)")
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1, 0.5, 1.0, 1.5, 2.0, 2.5, 2.75])
     ap.add_argument("--F", type=float, default=None, help="Froude number of the supercritical case (3)")
@@ -252,6 +325,13 @@ def main(argv=None):
     import __graft_entry__
     __graft_entry__.build()
     saved = {}
+    if a.case == "large":
+        rep = run_large(log=lambda m: print(m, file=sys.stderr, flush=True), max_newton=a.max_newton)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(rep, fh, indent=1)
+        print(json.dumps(rep))
+        return 0
     if a.case == "compare":
         def on_case(rep, eps, kind, nv):
             if a.out:

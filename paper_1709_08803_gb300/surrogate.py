@@ -44,6 +44,8 @@ def _lib():
         L.bfs_cno_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP]
         L.bfs_cno_read_loss.argtypes = [_VP, C(ctypes.c_float), _VP]
         L.bfs_cno_guess.argtypes = [_VP, _VP, _VP, _VP, _VP]
+        L.bfs_cno_solve.argtypes = [_VP, _VP, _VP, _VP, C(bfs.bfs_stats), C(ctypes.c_int), _VP]
+        L.bfs_cno_solve_host.argtypes = [_VP, _VP, _VP, _VP, C(bfs.bfs_stats), C(ctypes.c_int), _VP]
         L._cno_ready = True
     return L
 
@@ -158,6 +160,38 @@ class CNO:
         self._check(_lib().bfs_cno_read_loss(self._n, ctypes.byref(v), bfs._stream(None)))
         return v.value
 
+    def solve(self, ctx: bfs.Context, x, u, stream=None):
+        """Solve from the network's guess for features x (CUDA float32 [1, M, N, 4])
+        into the device vector u, the uniform stream as fallback; returns the
+        summed stats with 'fallback' (the final status is in 'status')."""
+        self._images(x, 4, 1)
+        st = bfs.bfs_stats()
+        fb = ctypes.c_int()
+        rc = _lib().bfs_cno_solve(self._n, ctx._ctx, _VP(x.data_ptr()), ctx._vec(u), ctypes.byref(st),
+                                  ctypes.byref(fb), bfs._stream(stream))
+        if rc not in (0, bfs.BFS_ENOCONV, bfs.BFS_ELINESEARCH, bfs.BFS_EBREAKDOWN, bfs.BFS_ENAN, bfs.BFS_ETIMEOUT):
+            self._check(rc)
+        d = st.as_dict()
+        d["fallback"] = bool(fb.value)
+        return d
+
+    def solve_host(self, ctx: bfs.Context, x_host: np.ndarray, u_host: np.ndarray, stream=None):
+        """solve on host buffers: features x_host (float32 [M, N, 4] or [1, M, N, 4],
+        C-contiguous) in, the solution into u_host (float64, n); both copies in the call."""
+        if x_host.dtype != np.float32 or not x_host.flags["C_CONTIGUOUS"] or x_host.size != self.H * self.W * 4:
+            raise ValueError("x_host: C-contiguous float32 with M*N*4 values")
+        if u_host.dtype != np.float64 or not u_host.flags["C_CONTIGUOUS"] or u_host.size != ctx.n:
+            raise ValueError("u_host: C-contiguous float64 of the context's length")
+        st = bfs.bfs_stats()
+        fb = ctypes.c_int()
+        rc = _lib().bfs_cno_solve_host(self._n, ctx._ctx, _VP(x_host.ctypes.data), _VP(u_host.ctypes.data),
+                                       ctypes.byref(st), ctypes.byref(fb), bfs._stream(stream))
+        if rc not in (0, bfs.BFS_ENOCONV, bfs.BFS_ELINESEARCH, bfs.BFS_EBREAKDOWN, bfs.BFS_ENAN, bfs.BFS_ETIMEOUT):
+            self._check(rc)
+        d = st.as_dict()
+        d["fallback"] = bool(fb.value)
+        return d
+
     def guess(self, ctx: bfs.Context, x, u=None):
         """Unknown vector for ctx from features x (CUDA float32 [1, M, N, 4])."""
         import torch
@@ -224,10 +258,12 @@ def solve_with_continuation(ctx, topo, u0=None, stages=(1.0 / 3.0, 2.0 / 3.0, 1.
 
 def bin_context(ctxs, mesh, topo, F, opts, bin_width=0.02):
     """A context for F from the per-bin cache (one factored preconditioner per
-    bin of Froude numbers; F itself is set exactly)."""
+    bin of Froude numbers; F itself is set exactly).  opts: options, or a
+    function of the bin's Froude number returning them."""
     key = int(F / bin_width)
     if key not in ctxs:
-        c = bfs.Context(mesh, topo, (key + 0.5) * bin_width, opts)
+        Fb = (key + 0.5) * bin_width
+        c = bfs.Context(mesh, topo, Fb, opts(Fb) if callable(opts) else opts)
         c.precond_factor()
         ctxs[key] = c
     c = ctxs[key]
@@ -235,13 +271,17 @@ def bin_context(ctxs, mesh, topo, F, opts, bin_width=0.02):
     return c
 
 
-def solver_options(tol: float = 1e-8, budget_s: float = 3.0):
-    """The mixed form with early exits: GMRES capped at 80 iterations per
-    Newton step and the solve abandoned after 3 consecutive Newton steps whose
-    GMRES ended above tolerance (most draws near F = 1 or with wide bumps have
-    no steady solution; this makes a failed attempt cost ~0.2 s, not seconds)."""
+def solver_options(tol: float = 1e-8, budget_s: float = 3.0, F: float | None = None):
+    """The mixed form with early exits: GMRES capped per Newton step (80
+    iterations for subcritical F; 400 for supercritical F, whose solves need
+    50-600 with the linear preconditioner) and the solve abandoned after 3
+    consecutive Newton steps whose GMRES ended above tolerance (most draws near
+    F = 1 or with wide bumps have no steady solution; this makes a failed
+    attempt cost a fraction of a second, not seconds)."""
+    sup = F is not None and F > 1.0
     return bfs.default_options(tol=tol, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=1e-2, max_newton=25, max_krylov=80, time_budget_s=budget_s,
+                               eta=1e-2, max_newton=25, max_krylov=400 if sup else 80,
+                               time_budget_s=2.0 * budget_s if sup else budget_s,
                                precond_precision=bfs.BFS_FP32C, refine_below=1e-5, stall_newton=3, forcing=1)
 
 
@@ -281,7 +321,7 @@ def generate(n: int, seed: int, mesh=None, tol: float = 1e-8, time_budget_s: flo
     xs = np.zeros((n, mesh.M, mesh.N, 4), dtype=np.float32)
     ys = np.zeros((n, mesh.M, mesh.N, 3), dtype=np.float32)
     recs, ctxs = [], {}
-    opts = solver_options(tol)
+    opts = lambda Fb: solver_options(tol, F=Fb)
     xg = torch.tensor(mesh.x(), device="cuda").view(1, -1)
     t0 = time.time()
     k = 0

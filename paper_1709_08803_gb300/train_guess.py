@@ -28,8 +28,8 @@ import numpy as np
 
 
 def evaluate(params, scale, n_test: int, seed: int, log=print):
-    """n_test held-out draws (attempts, converged or not) of the same distribution."""
-    """Held-out problems, three arms: the network's guess (one direct solve;
+    """n_test held-out draws (attempts, converged or not) of the same
+    distribution, three arms: the network's guess (one direct solve;
     continuation from the uniform stream if it fails), continuation from the
     uniform stream (the baseline; a direct solve is tried first), and a single
     direct solve from the uniform stream.  Costs are summed over every solve an
@@ -44,7 +44,7 @@ def evaluate(params, scale, n_test: int, seed: int, log=print):
     probs = [S.sample_problem_desc(rng, mesh) for _ in range(n_test)]
     net = S.CNO(mesh.M, mesh.N, 1)
     net.set_params(params, scale)
-    opts = S.solver_options()
+    opts = lambda Fb: S.solver_options(F=Fb)
     ctxs, rows = {}, []
     for i, (topo, F, desc) in enumerate(probs):
         c = S.bin_context(ctxs, mesh, topo, F, opts)
