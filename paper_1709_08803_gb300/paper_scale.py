@@ -78,9 +78,13 @@ def wake_metrics(x, y, zeta, zeta_x, zeta_y, x_from: float = 15.0, x_to: float =
 
 def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: int = 40, log=print,
         F: float | None = None, on_stage=None, refine_below: float = 1e-5, max_krylov: int = 400,
-        u0=None):
+        u0=None, eps0: float | None = None, u_prev=None, eps_prev: float | None = None, secant: bool = True):
     """Continuation in eps from the uniform stream, or from u0 (an unknown
-    vector of a converged earlier stage, host array)."""
+    vector of a converged earlier stage at eps0, host array).  With secant,
+    each stage after the second starts from the secant prediction through the
+    two previous converged stages, u_k + (u_k - u_{k-1}) (eps - eps_k) /
+    (eps_k - eps_{k-1}), instead of u_k alone (u_prev/eps_prev: the stage
+    before u0, if known)."""
     import torch
 
     from . import bfs
@@ -104,12 +108,17 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
     log(f"{case} 281x281 F={F0}: {ctx.n} unknowns, {ctx.pair_evals:.3e} pair evaluations per residual, "
         f"preconditioner (half band {half_band}) factored in {factor_s:.1f} s")
     u = ctx.flat_guess() if u0 is None else torch.tensor(np.asarray(u0, dtype=np.float64), device="cuda")
+    last = (eps0, u.clone()) if u0 is not None else None
+    before = (eps_prev, torch.tensor(np.asarray(u_prev, dtype=np.float64), device="cuda")) \
+        if (u_prev is not None and eps_prev is not None) else None
     stages = []
     rep = {"case": case, "mesh": "281x281", "F": F0, "half_band": half_band, "factor_s": factor_s,
            "unknowns": mesh.n_unknowns, "pair_evals_per_residual": mesh.pair_evals(), "stages": stages}
     for eps in eps_list:
         _, topo_e, _ = cfg(eps)
         ctx.set_topography(topo_e)
+        if secant and last is not None and before is not None and last[0] != before[0]:
+            u.copy_(last[1] + (last[1] - before[1]) * ((eps - last[0]) / (last[0] - before[0])))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = ctx.solve(u, raise_on_error=False)
@@ -130,6 +139,7 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
             on_stage(rep, eps, nv, u.cpu().numpy() if st["status"] == 0 else None)
         if st["status"] != 0:
             break
+        before, last = last, (eps, u.clone())
     ctx.close()
     return rep
 
@@ -309,6 +319,7 @@ def main(argv=None):
                     help="|F|inf below which the Newton residuals switch to double-float")
     ap.add_argument("--save-u", default=None, help="unknown vector of the last converged stage (.npz)")
     ap.add_argument("--start-u", default=None, help="start from a --save-u file instead of the uniform stream")
+    ap.add_argument("--no-secant", action="store_true", help="start each stage from the previous solution only")
     ap.add_argument("--out", default=None, help="report (JSON), rewritten after every stage")
     ap.add_argument("--fields", default=None, help="surface fields of every converged stage (.npz)")
     ap.add_argument("--analyse", default=None,
@@ -355,17 +366,25 @@ def main(argv=None):
             for k in ("zeta", "zeta_x", "zeta_y"):
                 saved[f"{k}_eps{eps:g}"] = nv[k]
             np.savez_compressed(a.fields, **saved)
-        if a.save_u and u is not None:
-            np.savez_compressed(a.save_u, u=u, eps=eps, F=rep["F"], case=rep["case"])
+        if a.save_u and u is not None:  # the last two converged stages (for a secant restart)
+            prev = saved_u.get("last")
+            saved_u["last"] = (u, eps)
+            extra = {"u_prev": prev[0], "eps_prev": prev[1]} if prev is not None else {}
+            np.savez_compressed(a.save_u, u=u, eps=eps, F=rep["F"], case=rep["case"], **extra)
 
-    u0 = None
+    u0, eps0, u_prev, eps_prev = None, None, None, None
+    saved_u = {}
     if a.start_u:
         d = np.load(a.start_u)
-        u0 = d["u"]
-        print(f"starting from {a.start_u} (eps = {float(d['eps']):g})", file=sys.stderr, flush=True)
+        u0, eps0 = d["u"], float(d["eps"])
+        if "u_prev" in d.files:
+            u_prev, eps_prev = d["u_prev"], float(d["eps_prev"])
+            saved_u["last"] = (u0, eps0)
+        print(f"starting from {a.start_u} (eps = {eps0:g})", file=sys.stderr, flush=True)
     rep = run(a.case, a.eps, a.half_band, max_newton=a.max_newton,
               log=lambda m: print(m, file=sys.stderr, flush=True), F=a.F, on_stage=on_stage,
-              refine_below=a.refine_below, max_krylov=a.max_krylov, u0=u0)
+              refine_below=a.refine_below, max_krylov=a.max_krylov, u0=u0, eps0=eps0, u_prev=u_prev,
+              eps_prev=eps_prev, secant=not a.no_secant)
     print(json.dumps(rep))
     return 0
 
