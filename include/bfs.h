@@ -294,6 +294,23 @@ int bfs_sweep_schedule(int M, int half_band, int twisted, int *tasks_out, int ca
    sweeps and the task multiplies at least one block. */
 int bfs_debug_stall_sweep(bfs_ctx *ctx, int task);
 
+/* The inversions of the block factorisation (App. B: the inverted diagonal
+   blocks D_k^-1 of the block LU, and the two-ended order's middle system) on
+   caller matrices.  A: DEVICE, nmat (1 or 2) consecutive n x n row-major FP64
+   matrices, read only; Ainv: DEVICE, the same layout, receives the inverses.
+   method 0: FP64 Gauss-Jordan with partial pivoting, rows spread over the
+   GPU, one exchange between CTAs per column (the factorisation's kernel when
+   the sweeps are FP64); method 1: blocked Gauss-Jordan in double-float
+   arithmetic (panels of up to 64 columns in one CTA's shared memory, then one
+   rank-panel product per panel; the kernel when the sweeps are FP32).  The
+   pivots are the same in both (the unused row with the largest |entry|, ties
+   to the lowest row).  Allocates its own scratch and synchronises stream.
+   BFS_EINVAL for a bad argument or an n the method's tiles do not take
+   (method 0: n > 16 rows per CTA; method 1: a panel of 8 columns does not
+   fit in shared memory, n > about 3500), BFS_ESINGULAR for a zero pivot,
+   BFS_ETIMEOUT if a wait between CTAs gave up (method 0). */
+int bfs_gj_invert(const double *A, double *Ainv, int n, int nmat, int method, void *stream);
+
 /* Profiling.  bfs_profile_enable(ctx, 1) records a CUDA event pair on the
    launching stream around every pair-kernel launch and every preconditioner
    apply of the context; bfs_profile_read waits for the recorded events and

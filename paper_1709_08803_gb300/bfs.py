@@ -131,6 +131,7 @@ def lib():
         L.bfs_debug_stall_sweep.argtypes = [_VP, ctypes.c_int]
         L.bfs_precond_info.argtypes = [_VP, C(ctypes.c_int)]
         L.bfs_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _VP, _VP, C(ctypes.c_double)]
+        L.bfs_gj_invert.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         _lib = L
     return _lib
 
@@ -385,6 +386,21 @@ def peak_probe(kind: int, iters: int, out, stream=None) -> float:
     if rc:
         raise BfsError(rc, "peak probe failed")
     return ops.value
+
+
+def gj_invert(A, method: int, stream=None):
+    """Inverses of the (n, n) or (2, n, n) float64 CUDA tensor A by the
+    factorisation's Gauss-Jordan kernels (method 0: FP64 rows kernel, 1:
+    blocked double-float); raises BfsError on a failure code."""
+    import torch
+    A = A.contiguous()
+    nmat = 1 if A.dim() == 2 else A.shape[0]
+    out = torch.empty_like(A)
+    rc = lib().bfs_gj_invert(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(A.shape[-1]),
+                             int(nmat), int(method), _stream(stream))
+    if rc != BFS_OK:
+        raise BfsError(rc, f"bfs_gj_invert(n={A.shape[-1]}, nmat={nmat}, method={method})")
+    return out
 
 
 def peak_probe_threads() -> int:

@@ -34,6 +34,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "bfs_internal.cuh"
@@ -680,6 +681,329 @@ __global__ void __launch_bounds__(256) k_dfgemm(GemmBatch gb, int n, double alph
     }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan inversion in double-float, for the factors of the
+// FP32-swept preconditioner (whose own rounding, 2^-24, is far above the
+// 2^-46 of the arithmetic here).  Columns are taken in panels of bw: one CTA
+// per matrix runs the bw elimination steps on the n x bw panel alone, with the
+// rows resident in shared memory as hi/lo float pairs and the same implicit
+// partial pivoting as k_gj_rows (pivot of column k: the unused row with the
+// largest |S[i][k]|, ties to the lowest row; rows never move).  The steps of a
+// panel multiply the matrix from the left by E = I + sum_j (v_j - e_pj) e_pj^T
+// (p_j its pivot rows, v_j the scaled elimination column of step j), and the
+// in-place storage leaves E[:, p_j] in panel column j.  So, with T the pivot
+// rows taken before the update,
+//     A[:, c] <- A[:, c] + (E[:, P] - I[:, P]) T[:, c]     (c outside the panel)
+// while the panel columns take E[:, P] itself.  The panel kernel writes
+// Pm = E[:, P] (n x bw) and Tm = T (bw x n, its panel columns replaced by the
+// identity), and zeroes the pivot rows and the panel columns of A; the
+// product A += Pm Tm (k_gjp_update) then completes the panel.  Per panel the
+// serial part is bw steps inside one CTA (two block barriers each) instead of
+// bw grid-wide exchanges; the rest is one rank-bw product over the whole GPU.
+// The result is read through perm / pinv as for k_gj_rows.
+// ---------------------------------------------------------------------------
+constexpr int GJP_TPB = 512, GJP_WARPS = GJP_TPB / 32, GJP_BMAX = 64;
+constexpr size_t GJP_SMEM = 225 * 1024;
+
+struct GjPanelArgs {
+    double *A0, *A1;  // the matrices, n x n row-major, inverted in place
+    double *P0, *P1;  // E[:, P] of the current panel, n x bw
+    double *T0, *T1;  // its pivot rows, bw x n
+    int *perm;        // [nmat][2 n]: pivot row of each column, then the inverse permutation
+    int n, k0, bw;
+    int *pivflag;
+};
+
+__device__ __forceinline__ float2 df2_split(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ double df2_join(float2 a) { return (double)a.x + (double)a.y; }
+
+// a b in double-float (two-product by fused multiply-add; lo*lo dropped)
+__device__ __forceinline__ float2 df2_mul(float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float h = __fadd_rn(p, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// s - a b in double-float: Knuth's two-sum of s.hi and the rounded product,
+// the product's error and s.lo into the low part, then renormalised
+__device__ __forceinline__ float2 df2_fms(float2 s, float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float t = __fsub_rn(s.x, p);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fsub_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fadd_rn(p, bb));
+    const float l = __fadd_rn(__fsub_rn(s.y, e), err);
+    const float h = __fadd_rn(t, l);
+    return make_float2(h, __fsub_rn(l, __fsub_rn(h, t)));
+}
+
+__device__ __forceinline__ void gjp_best(float &v, int &r, float ov, int orr)
+{
+    if (orr >= 0 && (r < 0 || ov > v || (ov == v && orr < r))) { v = ov; r = orr; }
+}
+
+// One panel.  BW: the allocated panel width (16, 32 or 64; the last panel of a
+// matrix may use fewer columns, bw <= BW).  Lanes own columns (a lane holds
+// columns lane and lane + 32 when BW = 64; half-warps take two rows at once
+// when BW = 16), warps own rows.  A step has three phases between block
+// barriers: (1) every thread copies its rows' entries of column j to fcol,
+// zeroes them in S and offers the largest unused one as a pivot candidate;
+// (2) warp 0 picks the pivot p, forms 1/a in double-float from an FP32
+// reciprocal and one Newton step, and scales the pivot row into pr;
+// (3) every row takes S[i][c] - fcol[i] pr[c], which with S[i][j] = 0 is also
+// the elimination column -f_i / a, and the thread that owns row p then
+// overwrites it with pr.  Phase 3 keeps the thread's columns of pr in
+// registers and updates GJP_U rows at a time, loads first, so that the
+// dependent double-float chains of several rows overlap.
+constexpr int GJP_U = 4;
+
+// 1 / a in double-float: the FP32 reciprocal y0 and one Newton step,
+// y0 + y0 (1 - a y0), the residual formed exactly by df2_fms
+__device__ __forceinline__ float2 df2_recip(float2 a)
+{
+    const float y0 = __frcp_rn(a.x);
+    const float2 r = df2_fms(make_float2(1.f, 0.f), a, make_float2(y0, 0.f));
+    const float c = __fmul_rn(y0, r.x);
+    const float h = __fadd_rn(y0, c);
+    return make_float2(h, __fsub_rn(c, __fsub_rn(h, y0)));
+}
+
+template <int BW>
+__global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
+{
+    constexpr int TPR = BW >= 32 ? 32 : BW;     // threads per row
+    constexpr int NC = BW >= 32 ? BW / 32 : 1;  // columns per thread
+    constexpr int RPW = 32 / TPR;               // rows per warp and pass
+    constexpr int RSTEP = GJP_WARPS * RPW;      // rows per CTA and pass
+    extern __shared__ float2 ps[];  // S: n BW, fcol: n, pr: GJP_BMAX; then used: n bytes
+    __shared__ float cv[GJP_WARPS];
+    __shared__ int ci[GJP_WARPS];
+    __shared__ int prow[GJP_BMAX];
+    const int mat = blockIdx.x, n = a.n, k0 = a.k0, bw = a.bw;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cl = lane % TPR, r0 = warp * RPW + lane / TPR;
+    // this thread's rows: r0, r0 + RSTEP, ...; nfull of them in whole groups of GJP_U
+    const int nrow = r0 < n ? (n - r0 + RSTEP - 1) / RSTEP : 0;
+    const int nfull = nrow - nrow % GJP_U;
+    double *A = mat ? a.A1 : a.A0;
+    double *Pm = mat ? a.P1 : a.P0;
+    double *Tm = mat ? a.T1 : a.T0;
+    int *perm = a.perm + (size_t)mat * 2 * n;
+    float2 *S = ps, *fcol = ps + (size_t)n * BW, *pr = fcol + n;
+    unsigned char *used = reinterpret_cast<unsigned char *>(pr + GJP_BMAX);
+    for (int i = tid; i < n; i += GJP_TPB) used[i] = 0;
+    __syncthreads();
+    for (int q = tid; q < k0; q += GJP_TPB) used[perm[q]] = 1;
+    // the panel into shared memory, GJP_U rows of loads in flight per thread
+    for (int ib = r0; ib < n; ib += GJP_U * RSTEP) {
+        double v[GJP_U][NC];
+#pragma unroll
+        for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const int i = ib + u * RSTEP, col = cl + c * 32;
+                v[u][c] = (i < n && col < bw) ? A[(size_t)i * n + k0 + col] : 0.0;
+            }
+#pragma unroll
+        for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const int i = ib + u * RSTEP, col = cl + c * 32;
+                if (i < n) S[(size_t)i * BW + col] = df2_split(v[u][c]);
+            }
+    }
+    __syncthreads();
+    for (int j = 0; j < bw; j++) {
+        {  // (1) column j out to fcol and zeroed; the pivot candidates
+            float v = -1.f;
+            int r = -1;
+            for (int i = tid; i < n; i += GJP_TPB) {
+                const float2 x = S[(size_t)i * BW + j];
+                fcol[i] = x;
+                S[(size_t)i * BW + j] = make_float2(0.f, 0.f);
+                if (!used[i]) gjp_best(v, r, fabsf(x.x), i);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, v, o);
+                const int orr = __shfl_down_sync(0xffffffffu, r, o);
+                gjp_best(v, r, ov, orr);
+            }
+            if (lane == 0) { cv[warp] = v; ci[warp] = r; }
+        }
+        __syncthreads();
+        if (warp == 0) {  // (2) the pivot, 1/a and the scaled pivot row
+            float v = lane < GJP_WARPS ? cv[lane] : -1.f;
+            int r = lane < GJP_WARPS ? ci[lane] : -1;
+            for (int o = GJP_WARPS / 2; o > 0; o >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, v, o);
+                const int orr = __shfl_down_sync(0xffffffffu, r, o);
+                gjp_best(v, r, ov, orr);
+            }
+            const int p = max(__shfl_sync(0xffffffffu, r, 0), 0);
+            const float2 piv = fcol[p];
+            const float2 inv = piv.x != 0.f ? df2_recip(piv) : make_float2(0.f, 0.f);
+            for (int c = lane; c < bw; c += 32) pr[c] = c == j ? inv : df2_mul(S[(size_t)p * BW + c], inv);
+            if (lane == 0) {
+                if (piv.x == 0.f) atomicOr(a.pivflag, 1);
+                used[p] = 1;
+                prow[j] = p;
+                perm[k0 + j] = p;
+            }
+        }
+        __syncthreads();
+        // (3) every row: S[i][c] -= f_i pr[c]; then the pivot row takes pr
+        const int p = prow[j];
+        float2 prv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) prv[c] = cl + c * 32 < bw ? pr[cl + c * 32] : make_float2(0.f, 0.f);
+        float2 *Sc = S + (size_t)r0 * BW + cl;
+        const float2 *fc = fcol + r0;
+        for (int q = 0; q < nfull; q += GJP_U) {
+            float2 sv[GJP_U][NC], fv[GJP_U];
+#pragma unroll
+            for (int u = 0; u < GJP_U; u++) {
+                fv[u] = fc[(size_t)(q + u) * RSTEP];
+#pragma unroll
+                for (int c = 0; c < NC; c++) sv[u][c] = Sc[(size_t)(q + u) * RSTEP * BW + c * 32];
+            }
+#pragma unroll
+            for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+                for (int c = 0; c < NC; c++) sv[u][c] = df2_fms(sv[u][c], fv[u], prv[c]);
+#pragma unroll
+            for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+                for (int c = 0; c < NC; c++) Sc[(size_t)(q + u) * RSTEP * BW + c * 32] = sv[u][c];
+        }
+        for (int q = nfull; q < nrow; q++) {
+            const float2 f = fc[(size_t)q * RSTEP];
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                float2 *e = Sc + (size_t)q * RSTEP * BW + c * 32;
+                *e = df2_fms(*e, f, prv[c]);
+            }
+        }
+        if (p >= r0 && (p - r0) % RSTEP == 0)
+#pragma unroll
+            for (int c = 0; c < NC; c++) S[(size_t)p * BW + cl + c * 32] = prv[c];
+        __syncthreads();
+    }
+    // E[:, P] out (ld bw); the pivot rows out (panel columns: the identity), then zeroed
+    for (int i = r0; i < n; i += RSTEP)
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            const int col = cl + c * 32;
+            if (col < bw) Pm[(size_t)i * bw + col] = df2_join(S[(size_t)i * BW + col]);
+        }
+    for (int jr = warp; jr < bw; jr += GJP_WARPS) {
+        const double *src = A + (size_t)prow[jr] * n;
+        double *dst = Tm + (size_t)jr * n;
+        for (int cb = lane; cb < n; cb += 8 * 32) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int col = cb + q * 32;
+                v[q] = col < n ? src[col] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int col = cb + q * 32, c2 = col - k0;
+                if (col < n) dst[col] = (c2 >= 0 && c2 < bw) ? (c2 == jr ? 1.0 : 0.0) : v[q];
+            }
+        }
+    }
+    __syncthreads();
+    for (int jr = warp; jr < bw; jr += GJP_WARPS) {
+        double *row = A + (size_t)prow[jr] * n;
+        for (int col = lane; col < n; col += 32) row[col] = 0.0;
+    }
+    for (int i = r0; i < n; i += RSTEP)
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            const int col = cl + c * 32;
+            if (col < bw) A[(size_t)i * n + k0 + col] = 0.0;
+        }
+    if (k0 + bw == n) {  // last panel: the inverse permutation
+        __syncthreads();
+        for (int k = tid; k < n; k += GJP_TPB) perm[n + perm[k]] = k;
+    }
+}
+
+// A += Pm Tm (n x bw by bw x n) for one or two matrices (blockIdx.z), in
+// 32 x 32 tiles (many CTAs per SM: one rank-bw product is a few microseconds
+// of work): the whole bw extent of both operands is staged once as hi/lo
+// float pairs, then each thread forms 2 x 2 entries with the double-float
+// products and sums of k_dfgemm and rounds each pair once into its FP64 entry.
+constexpr int GU_T = 32;
+
+__global__ void __launch_bounds__(256) k_gjp_update(GjPanelArgs a)
+{
+    __shared__ float Ah[GJP_BMAX][GU_T + 1], Al[GJP_BMAX][GU_T + 1];
+    __shared__ float Bh[GJP_BMAX][GU_T], Bl[GJP_BMAX][GU_T];
+    const int n = a.n, bw = a.bw;
+    double *C = blockIdx.z ? a.A1 : a.A0;
+    const double *P = blockIdx.z ? a.P1 : a.P0;
+    const double *T = blockIdx.z ? a.T1 : a.T0;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int row0 = blockIdx.y * GU_T, col0 = blockIdx.x * GU_T;
+    for (int e = threadIdx.x; e < GU_T * bw; e += 256) {
+        const int r = e / bw, kk = e - r * bw, gr = row0 + r;
+        const double v = gr < n ? P[(size_t)gr * bw + kk] : 0.0;
+        const float h = (float)v;
+        Ah[kk][r] = h;
+        Al[kk][r] = (float)(v - (double)h);
+    }
+    for (int e = threadIdx.x; e < GU_T * bw; e += 256) {
+        const int kk = e / GU_T, cc = e - kk * GU_T, gc = col0 + cc;
+        const double v = gc < n ? T[(size_t)kk * n + gc] : 0.0;
+        const float h = (float)v;
+        Bh[kk][cc] = h;
+        Bl[kk][cc] = (float)(v - (double)h);
+    }
+    __syncthreads();
+    float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int kk = 0; kk < bw; kk++) {
+        const float ah[2] = {Ah[kk][ty * 2], Ah[kk][ty * 2 + 1]}, al[2] = {Al[kk][ty * 2], Al[kk][ty * 2 + 1]};
+        const float bh[2] = {Bh[kk][tx * 2], Bh[kk][tx * 2 + 1]}, bl[2] = {Bl[kk][tx * 2], Bl[kk][tx * 2 + 1]};
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const float p = __fmul_rn(ah[i], bh[j]);
+                float e = fmaf(ah[i], bh[j], -p);
+                e = fmaf(ah[i], bl[j], e);
+                e = fmaf(al[i], bh[j], e);
+                const float sm = __fadd_rn(hi[i][j], p);
+                const float bp = __fsub_rn(sm, hi[i][j]);
+                const float err = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(sm, bp)), __fsub_rn(p, bp));
+                hi[i][j] = sm;
+                lo[i][j] = __fadd_rn(lo[i][j], __fadd_rn(err, e));
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int gr = row0 + ty * 2 + i;
+        if (gr >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int gc = col0 + tx * 2 + j;
+            if (gc < n) C[(size_t)gr * n + gc] += (double)hi[i][j] + (double)lo[i][j];
+        }
+    }
+}
+
 // Batched block products of the factorisation: FP64 when the sweeps are FP64,
 // double-float when they sweep FP32 copies of the factors (whose own rounding
 // is 2^-24, so the factors' 2^-46 is far below what the sweeps see).
@@ -1004,6 +1328,60 @@ static int gj_rows_invert(bfs_ctx *c, double *const *work, double *const *dst, i
     return BFS_OK;
 }
 
+// In-place inversion of one or two n x n matrices (row-major, contiguous) by
+// the blocked double-float kernels, results gathered into dst[i].  Returns 1
+// if a panel of 8 columns does not fit in shared memory (the caller falls
+// back).  Scratch: the perm / pinv words after the slots of d_gjscr, Pm and Tm
+// in d_gjdata.
+static int gj_panel_invert(bfs_ctx *c, double *const *work, double *const *dst, int nmat, int n, cudaStream_t s)
+{
+    // widest panel whose rows fit: BW columns of float pairs per row, plus fcol,
+    // the pivot row and the used flags
+    auto fits = [&](int bwid) {
+        return sizeof(float2) * ((size_t)n * bwid + n + GJP_BMAX) + (size_t)n <= GJP_SMEM;
+    };
+    const int BW = fits(64) ? 64 : fits(32) ? 32 : fits(16) ? 16 : 0;
+    if (!BW) return 1;
+    const void *fn = BW == 64 ? (const void *)k_gjp_panel<64>
+                   : BW == 32 ? (const void *)k_gjp_panel<32> : (const void *)k_gjp_panel<16>;
+    BFS_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJP_SMEM));
+    const size_t smem = sizeof(float2) * ((size_t)n * BW + n + GJP_BMAX) + (size_t)n;
+    GjPanelArgs a;
+    a.A0 = work[0];
+    a.A1 = nmat > 1 ? work[1] : work[0];
+    double *pt = c->d_gjdata;
+    a.P0 = pt;
+    a.T0 = pt + (size_t)n * BW;
+    a.P1 = nmat > 1 ? pt + 2 * (size_t)n * BW : a.P0;
+    a.T1 = nmat > 1 ? pt + 3 * (size_t)n * BW : a.T0;
+    a.perm = reinterpret_cast<int *>(static_cast<unsigned long long *>(c->d_gjscr) + 4 * (size_t)num_sms(c->device));
+    a.n = n;
+    a.pivflag = c->d_pivflag;
+    const dim3 ug((n + GU_T - 1) / GU_T, (n + GU_T - 1) / GU_T, nmat);
+    for (int k0 = 0; k0 < n; k0 += BW) {
+        a.k0 = k0;
+        a.bw = std::min(BW, n - k0);
+        if (BW == 64) k_gjp_panel<64><<<nmat, GJP_TPB, smem, s>>>(a);
+        else if (BW == 32) k_gjp_panel<32><<<nmat, GJP_TPB, smem, s>>>(a);
+        else k_gjp_panel<16><<<nmat, GJP_TPB, smem, s>>>(a);
+        k_gjp_update<<<ug, 256, 0, s>>>(a);
+        c->launches += 2;
+    }
+    for (int i = 0; i < nmat; i++) {
+        k_gj_unperm<<<1024, 256, 0, s>>>(work[i], a.perm + (size_t)i * 2 * n, dst[i], n);
+        c->launches++;
+    }
+    BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// Scratch doubles of d_gjdata for matrices of up to nmax rows: the candidate
+// rows of k_gj_rows (2 parities x CTAs) or Pm and Tm of two blocked inversions.
+static size_t gj_data_doubles(int sms, int nmax)
+{
+    return std::max<size_t>(2 * (size_t)sms, 4 * (size_t)GJP_BMAX) * (size_t)nmax;
+}
+
 int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
 {
     int h = half_band >= 0 ? half_band : c->opt.half_band;
@@ -1035,7 +1413,7 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
         const int G = num_sms(c->device), nmax = std::max(nb, twist >= 0 ? h * nb : nb);
         BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjscr, sizeof(unsigned long long) * 4 * (size_t)G +
                                                     sizeof(int) * 4 * (size_t)nmax));
-        BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjdata, sizeof(double) * 2 * (size_t)G * nmax));
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjdata, sizeof(double) * gj_data_doubles(G, nmax)));
     }
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int) * 8));  // [0] pivot flag, [4..5] grid barrier
     BFS_CUDA_TRY(c, cudaMalloc(&c->d_perm_a, sizeof(double) * 2 * (size_t)c->n));
@@ -1059,6 +1437,8 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
 
     auto B = [&](int l, int m) { return c->d_pc + ((size_t)l * nd + (m - l + h)) * bsz; };
     double *tmp = c->d_gj + gj_doubles;
+    // FP32 sweeps: blocked double-float inversions (FP64 ones otherwise)
+    const bool df = c->opt.precond_precision == BFS_FP32C && c->opt.surface_tension == 0.0;
     // D_k^-1 in place for the one or two diagonal blocks listed
     auto invert_diag = [&](const int *ks, int cnt) -> int {
         {  // rows in shared memory, no grid barrier
@@ -1068,7 +1448,8 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
                 dst[i] = B(ks[i], ks[i]);
                 BFS_CUDA_TRY(c, cudaMemcpyAsync(work[i], dst[i], sizeof(double) * bsz, cudaMemcpyDeviceToDevice, s));
             }
-            const int r = gj_rows_invert(c, work, dst, cnt, nb, s);
+            int r = df ? gj_panel_invert(c, work, dst, cnt, nb, s) : 1;
+            if (r == 1) r = gj_rows_invert(c, work, dst, cnt, nb, s);
             if (r <= 0) return r;
         }
         GjSet set;
@@ -1169,7 +1550,8 @@ int precond_factor(bfs_ctx *c, int half_band, cudaStream_t s)
                     k_blk_put<<<512, 256, 0, s>>>(B(t0 + ia, t0 + ib), work, nb, hn, ia, ib);
                     c->launches++;
                 }
-            rc = gj_rows_invert(c, &work, &out, 1, hn, s);
+            rc = df ? gj_panel_invert(c, &work, &out, 1, hn, s) : 1;
+            if (rc == 1) rc = gj_rows_invert(c, &work, &out, 1, hn, s);
             if (rc < 0) return rc;
             if (rc == 0) {
                 for (int ia = 0; ia < h; ia++)
@@ -1271,3 +1653,46 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
 }
 
 }  // namespace bfs
+
+// The Gauss-Jordan kernels on caller matrices, with scratch of its own.
+extern "C" int bfs_gj_invert(const double *A, double *Ainv, int n, int nmat, int method, void *stream)
+{
+    if (!A || !Ainv || n < 1 || n > 16384 || nmat < 1 || nmat > 2 || (method != 0 && method != 1))
+        return BFS_EINVAL;
+    std::unique_ptr<bfs_ctx> c(new bfs_ctx{});
+    if (cudaGetDevice(&c->device) != cudaSuccess) return BFS_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int G = bfs::num_sms(c->device);
+    const size_t nn = (size_t)n * n;
+    double *work = nullptr;
+    auto run = [&]() -> int {
+        BFS_CUDA_TRY(c, cudaMalloc(&work, sizeof(double) * nmat * nn));
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjscr, sizeof(unsigned long long) * 4 * (size_t)G + sizeof(int) * 4 * (size_t)n));
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_gjdata, sizeof(double) * bfs::gj_data_doubles(G, n)));
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_pivflag, sizeof(int) * 8));
+        BFS_CUDA_TRY(c, cudaMalloc(&c->d_flag, sizeof(int)));
+        BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_pivflag, 0, sizeof(int) * 8, s));
+        BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+        BFS_CUDA_TRY(c, cudaMemcpyAsync(work, A, sizeof(double) * nmat * nn, cudaMemcpyDeviceToDevice, s));
+        double *w[2] = {work, work + (nmat > 1 ? nn : 0)}, *d[2] = {Ainv, Ainv + (nmat > 1 ? nn : 0)};
+        int r = method == 1 ? bfs::gj_panel_invert(c.get(), w, d, nmat, n, s)
+                            : bfs::gj_rows_invert(c.get(), w, d, nmat, n, s);
+        if (r == 1) return BFS_EINVAL;
+        if (r) return r;
+        int fl[2] = {0, 0};
+        BFS_CUDA_TRY(c, cudaMemcpyAsync(&fl[0], c->d_pivflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BFS_CUDA_TRY(c, cudaMemcpyAsync(&fl[1], c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (fl[1] & 2) return BFS_ETIMEOUT;
+        if (fl[0]) return BFS_ESINGULAR;
+        return BFS_OK;
+    };
+    const int rc = run();
+    cudaStreamSynchronize(s);
+    cudaFree(work);
+    cudaFree(c->d_gjscr);
+    cudaFree(c->d_gjdata);
+    cudaFree(c->d_pivflag);
+    cudaFree(c->d_flag);
+    return rc;
+}

@@ -112,7 +112,7 @@ def run(case: str, eps_list, half_band: int = 3, tol: float = 1e-8, max_newton: 
     before = (eps_prev, torch.tensor(np.asarray(u_prev, dtype=np.float64), device="cuda")) \
         if (u_prev is not None and eps_prev is not None) else None
     stages = []
-    rep = {"case": case, "mesh": "281x281", "F": F0, "half_band": half_band, "factor_s": factor_s,
+    rep = {"case": case, "mesh": "281x281", "F": F0, "half_band": half_band, "tol": tol, "factor_s": factor_s,
            "unknowns": mesh.n_unknowns, "pair_evals_per_residual": mesh.pair_evals(), "stages": stages}
     for eps in eps_list:
         _, topo_e, _ = cfg(eps)
@@ -315,6 +315,8 @@ def main(argv=None):
     ap.add_argument("--half-band", type=int, default=3)
     ap.add_argument("--max-newton", type=int, default=40)
     ap.add_argument("--max-krylov", type=int, default=400)
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="|F|inf at which a stage has converged (KINSOL's default is about 6e-6)")
     ap.add_argument("--refine-below", type=float, default=1e-5,
                     help="|F|inf below which the Newton residuals switch to double-float")
     ap.add_argument("--save-u", default=None, help="unknown vector of the last converged stage (.npz)")
@@ -381,7 +383,7 @@ def main(argv=None):
             u_prev, eps_prev = d["u_prev"], float(d["eps_prev"])
             saved_u["last"] = (u0, eps0)
         print(f"starting from {a.start_u} (eps = {eps0:g})", file=sys.stderr, flush=True)
-    rep = run(a.case, a.eps, a.half_band, max_newton=a.max_newton,
+    rep = run(a.case, a.eps, a.half_band, tol=a.tol, max_newton=a.max_newton,
               log=lambda m: print(m, file=sys.stderr, flush=True), F=a.F, on_stage=on_stage,
               refine_below=a.refine_below, max_krylov=a.max_krylov, u0=u0, eps0=eps0, u_prev=u_prev,
               eps_prev=eps_prev, secant=not a.no_secant)
