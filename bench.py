@@ -321,9 +321,12 @@ def batch_summary(args, steps: int, warmup: int) -> dict:
 
     meshes, topos, Fs = W.config_batch(seed=3, B=args.batch)
     opts = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                               eta=args.eta, max_newton=30, max_krylov=80, time_budget_s=60.0,
+                               eta=args.eta, max_newton=30, max_krylov=400, time_budget_s=60.0,
                                precond_precision=_pc_prec(args), refine_below=args.refine_below,
                                stall_newton=3, forcing=args.forcing)
+    # max_krylov 400: the supercritical draws need 50-600 GMRES iterations per
+    # Newton step; stall_newton still abandons draws whose GMRES stalls above
+    # its tolerance in three consecutive Newton steps
     t0 = time.perf_counter()
     b = bfs.Batch(meshes, topos, Fs, opts)
     setup_s = time.perf_counter() - t0

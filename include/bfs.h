@@ -225,6 +225,17 @@ int bfs_precond_factor(bfs_ctx *ctx, int half_band, void *stream);
    FP64 sweeps).  BFS_ENOPREC before bfs_precond_factor. */
 int bfs_precond_info(const bfs_ctx *ctx, int *info4);
 
+/* How bfs_solve launched its Arnoldi steps (for tests and reports): info4[0]
+   step graphs instantiated (one per Krylov index and base residual buffer,
+   kept until a captured argument changes), info4[1] how many of them are
+   conditional (the step behind a device-side end-of-cycle flag, so the next
+   step is queued before the host reads this one's scalars), info4[2] 1 if
+   graphs are off for this context (a capture failed; steps launched one by
+   one), info4[3] 1 if a solve was handed the legacy default stream and ran on
+   the context's own stream (graphs cannot be captured on the legacy stream).
+   Profiling (bfs_profile_enable) launches steps one by one without graphs. */
+int bfs_solver_info(const bfs_ctx *ctx, int *info4);
+
 /* z = P^{-1} r with the factored preconditioner.  r, z: device, length n,
    in the order of u (r may equal z).  BFS_ENOPREC before bfs_precond_factor. */
 int bfs_precond_apply(bfs_ctx *ctx, const double *r, double *z, void *stream);
@@ -302,9 +313,9 @@ int bfs_debug_stall_sweep(bfs_ctx *ctx, int task);
    GPU, one exchange between CTAs per column (the factorisation's kernel when
    the sweeps are FP64); method 1: blocked Gauss-Jordan in double-float
    arithmetic (panels of up to 64 columns in one CTA's shared memory, then one
-   rank-panel product per panel; the kernel when the sweeps are FP32).  The
-   pivots are the same in both (the unused row with the largest |entry|, ties
-   to the lowest row).  Allocates its own scratch and synchronises stream.
+   rank-panel product per panel; the kernel when the sweeps are FP32).  Both
+   pivot on the unused row with the largest |entry|, ties to the lowest row;
+   method 1 compares the magnitudes to 12 significant bits.  Allocates its own scratch and synchronises stream.
    BFS_EINVAL for a bad argument or an n the method's tiles do not take
    (method 0: n > 16 rows per CTA; method 1: a panel of 8 columns does not
    fit in shared memory, n > about 3500), BFS_ESINGULAR for a zero pivot,

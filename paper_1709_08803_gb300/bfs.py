@@ -130,6 +130,7 @@ def lib():
                                          ctypes.c_int, C(ctypes.c_int)]
         L.bfs_debug_stall_sweep.argtypes = [_VP, ctypes.c_int]
         L.bfs_precond_info.argtypes = [_VP, C(ctypes.c_int)]
+        L.bfs_solver_info.argtypes = [_VP, C(ctypes.c_int)]
         L.bfs_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, _VP, _VP, C(ctypes.c_double)]
         L.bfs_gj_invert.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         _lib = L
@@ -255,6 +256,15 @@ class Context:
         info = (ctypes.c_int * 4)()
         self._check(lib().bfs_precond_info(self._ctx, info))
         return {"half_band": info[0], "twist": info[1], "chains": info[2], "sweep_steps": info[3]}
+
+    def solver_info(self) -> dict:
+        """How the solves of this context launched their Arnoldi steps: step
+        graphs instantiated, how many conditional (queued one step ahead),
+        whether graphs are off, whether the context's own stream was used."""
+        info = (ctypes.c_int * 4)()
+        self._check(lib().bfs_solver_info(self._ctx, info))
+        return {"step_graphs": info[0], "conditional": info[1], "graphs_off": bool(info[2]),
+                "own_stream": bool(info[3])}
 
     def debug_stall_sweep(self, task: int):
         """Test hook: the next FP32 sweep launch waits in `task` for a vector no

@@ -45,6 +45,15 @@ void free_all(bfs_ctx *c)
     cudaFree(c->d_giv);
     cudaFree(c->d_sbase);
     if (c->h_pin) cudaFreeHost(c->h_pin);
+    if (c->gm_ev) cudaEventDestroy(c->gm_ev);
+    c->gm_ev = nullptr;
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    c->join_ev = nullptr;
+    if (c->own_stream) {
+        cudaStreamSynchronize(c->own_stream);
+        cudaStreamDestroy(c->own_stream);
+    }
+    c->own_stream = nullptr;
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
 }
@@ -323,6 +332,22 @@ int bfs_precond_info(const bfs_ctx *c, int *info)
     info[1] = c->pc_twist;
     info[2] = c->sweep_table ? c->sweep_groups : (c->d_pc32 ? 1 : 0);
     info[3] = c->sweep_table ? std::max(c->sweep_ntask[0], c->sweep_ntask[1]) : 2 * c->M;
+    return BFS_OK;
+}
+
+int bfs_solver_info(const bfs_ctx *c, int *info)
+{
+    if (!c || !info) return BFS_EINVAL;
+    int graphs = 0, cond = 0;
+    for (size_t k = 0; k < c->gm_exec.size(); k++)
+        if (c->gm_exec[k]) {
+            graphs++;
+            cond += c->gm_iscond[k] ? 1 : 0;
+        }
+    info[0] = graphs;
+    info[1] = cond;
+    info[2] = c->gm_disabled;
+    info[3] = c->own_stream ? 1 : 0;
     return BFS_OK;
 }
 

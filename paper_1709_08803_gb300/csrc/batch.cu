@@ -470,13 +470,22 @@ int bfs_batch_solve(bfs_batch *b, double *const *u, bfs_stats *st, void *stream)
                 else if (g[i].state == bfs::Gm::RESTART) rst.push_back(i);
             }
             if (arn.empty() && rst.empty()) break;
-            for (int i : arn)
-                if ((rc = bfs::gm_arnoldi_pre(b->c[i], g[i], s))) return berr(b, rc, b->c[i]->err);
+            // the sweeps per instance, then |z|, h, u + h z for all in one launch pair
+            std::vector<bfs_ctx *> acs;
+            std::vector<bfs::Gm *> ags;
+            for (int i : arn) {
+                if ((rc = bfs::gm_arnoldi_sweep(b->c[i], g[i], s))) return berr(b, rc, b->c[i]->err);
+                acs.push_back(b->c[i]);
+                ags.push_back(&g[i]);
+            }
+            if (!arn.empty() && (rc = bfs::gm_multi_pre(acs.data(), ags.data(), (int)arn.size(), s)))
+                return berr(b, rc, acs[0]->err);
             live = arn;
             live.insert(live.end(), rst.begin(), rst.end());
             if ((rc = krylov_residuals(live))) return rc;
-            for (int i : arn)
-                if ((rc = bfs::gm_arnoldi_post(b->c[i], g[i], s))) return berr(b, rc, b->c[i]->err);
+            // Jz, CGS2, v_{j+1} and Givens for all in one cooperative launch
+            if (!arn.empty() && (rc = bfs::gm_multi_post(acs.data(), ags.data(), (int)arn.size(), s)))
+                return berr(b, rc, acs[0]->err);
             for (int i : rst)
                 if ((rc = bfs::gm_restart_post(b->c[i], g[i], s))) return berr(b, rc, b->c[i]->err);
             if ((rc = read_batch(b, live, 8, 2, s))) return rc;

@@ -145,6 +145,17 @@ struct bfs_ctx {
     // could change (factor, F, topography, surface pressure, u buffer)
     std::vector<cudaGraphExec_t> gm_exec;
     std::vector<unsigned long long> gm_nlaunch, gm_nflow;
+    // gm_iscond[key]: the step sits in a conditional node behind a guard that
+    // reads the device-side end-of-cycle flag, so the next step can be queued
+    // before this one's scalars reach the host; gm_cond: 1 while such graphs
+    // instantiate, -1 once one failed (plain step graphs from then on)
+    std::vector<char> gm_iscond;
+    int gm_cond;
+    cudaEvent_t gm_ev;
+    // solves handed the legacy default stream run here (graph capture needs a
+    // stream of its own), joined to the caller's stream by join_ev
+    cudaStream_t own_stream;
+    cudaEvent_t join_ev;
     const double *gm_u;
     int gm_warm, gm_disabled;
     int ldp32;                   // padded row length of d_pc32
@@ -207,6 +218,11 @@ void gm_start(bfs_ctx *c, Gm &g, const double *u, const double *F, const double 
               double fnorm2, double eta, int maxit, cudaStream_t s);
 void gm_cycle_begin(bfs_ctx *c, Gm &g, double beta, cudaStream_t s);
 int gm_arnoldi_pre(bfs_ctx *c, Gm &g, cudaStream_t s);
+int gm_arnoldi_sweep(bfs_ctx *c, Gm &g, cudaStream_t s);
+// several instances' Arnoldi steps at once (up to GM_BMAX per launch)
+constexpr int GM_BMAX = 64;
+int gm_multi_pre(bfs_ctx *const *cs, Gm *const *gs, int cnt, cudaStream_t s);
+int gm_multi_post(bfs_ctx *const *cs, Gm *const *gs, int cnt, cudaStream_t s);
 int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s);
 void gm_arnoldi_host(bfs_ctx *c, Gm &g, double hn, double res);
 int gm_cycle_end(bfs_ctx *c, Gm &g, cudaStream_t s);

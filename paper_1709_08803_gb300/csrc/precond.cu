@@ -539,6 +539,32 @@ __global__ void k_gj_get(const double *__restrict__ X, double *__restrict__ D, i
     }
 }
 
+// FP64 -> hi + lo FP32 pair by bit manipulation, with no FP64 arithmetic (the
+// FP64 pipe of this GPU retires two operations per clock per SM): hi keeps the
+// sign, the exponent and the top 23 stored mantissa bits (a truncation), lo
+// the remaining 29 bits rounded to FP32, so |v - hi - lo| <= 2^-48 |v| and
+// |lo| < 2^-23 |hi|.  |v| < 2^-126 gives 0 (and lo flushes to 0 below about
+// 2^-102: the kernels run with flush-to-zero); |v| >= 2^128, infinities and
+// NaN give an infinite or NaN hi.
+__device__ __forceinline__ float2 df2_split(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int hi32 = (unsigned int)(b >> 32), lo32 = (unsigned int)b;
+    const int e = (int)((hi32 >> 20) & 0x7ffu);
+    const unsigned int sgn = hi32 & 0x80000000u;
+    if (e < 897) return make_float2(__uint_as_float(sgn), 0.f);
+    if (e > 1150) {
+        const bool nan = e == 0x7ff && ((hi32 & 0xfffffu) | lo32);
+        return make_float2(__uint_as_float(sgn | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f);
+    }
+    const float h = __uint_as_float(sgn | ((unsigned int)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
+    const float r = __uint2float_rn(lo32 & 0x1fffffffu);
+    const int sc = e - 1075;  // weight of the last stored mantissa bit
+    const float l = sc >= -126 ? __fmul_rn(r, __uint_as_float((unsigned int)(sc + 127) << 23))
+                               : __fmul_rn(__fmul_rn(r, __uint_as_float((unsigned int)(sc + 191) << 23)), 0x1p-64f);
+    return make_float2(h, sgn ? -l : l);
+}
+
 // ---------------------------------------------------------------------------
 // Batched FP64 GEMM on nb x nb row-major blocks: C = alpha A B + beta C.
 // ---------------------------------------------------------------------------
@@ -602,8 +628,8 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmBatch gb, int n, double alpha
 
 // The same GEMM in double-float arithmetic on the FP32 pipes (about 40 T
 // lane-ops/s on GB300 against 0.6 T for FP64 FMA).  Each FP64 operand is split
-// as its tile is staged into an FP32 pair hi = fl(x), lo = fl(x - hi) (48
-// significant bits).  A product is hi*hi exactly -- the FMA returns the
+// as its tile is staged into an FP32 pair (df2_split: 48 significant bits, no
+// FP64 arithmetic).  A product is hi*hi exactly -- the FMA returns the
 // rounding error of the rounded product (Dekker) -- plus the cross terms
 // hi*lo + lo*hi in FP32; lo*lo, below 2^-48 of it, is dropped.  The running
 // sum is an unevaluated pair: Knuth's two-sum on the high parts, the errors and
@@ -611,44 +637,57 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmBatch gb, int n, double alpha
 // the product is FP64-grade for a preconditioner (relative error of order
 // K 2^-48).  The explicit _rn intrinsics keep the compiler from contracting
 // the product into the two-sum, which would break its exactness.
-__global__ void __launch_bounds__(256) k_dfgemm(GemmBatch gb, int n, double alpha, double beta)
+__global__ void __launch_bounds__(256, 3) k_dfgemm(GemmBatch gb, int n, double alpha, double beta)
 {
-    __shared__ float Ah[TK][TM + 1], Al[TK][TM + 1];
-    __shared__ float Bh[TK][TN + 1], Bl[TK][TN + 1];
+    // tiles [k][row] with rows padded to 68 floats: 16-byte aligned for the
+    // vector loads of the inner loop, and staging stores spread over the banks
+    constexpr int LD = TM + 4;
+    __shared__ __align__(16) float Ah[TK][LD], Al[TK][LD];
+    __shared__ __align__(16) float Bh[TK][LD], Bl[TK][LD];
     const double *A = gb.A[blockIdx.z], *B = gb.B[blockIdx.z];
     double *C = gb.C[blockIdx.z];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+    // staging map: A element (row ar + 16 q, k ak), B element (k bk + 4 q, col bc); q < 4
+    const int ak = tid % TK, ar = tid / TK, bc = tid % TN, bk = tid / TN;
+    double ra[4], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int gr = row0 + ar + 16 * q, gk = k0 + ak;
+            ra[q] = (gr < n && gk < n) ? A[(size_t)gr * n + gk] : 0.0;
+            const int gk2 = k0 + bk + 4 * q, gc = col0 + bc;
+            rb[q] = (gk2 < n && gc < n) ? B[(size_t)gk2 * n + gc] : 0.0;
+        }
+    };
+    auto stage = [&]() {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float2 a = df2_split(ra[q]), b = df2_split(rb[q]);
+            Ah[ak][ar + 16 * q] = a.x;
+            Al[ak][ar + 16 * q] = a.y;
+            Bh[bk + 4 * q][bc] = b.x;
+            Bl[bk + 4 * q][bc] = b.y;
+        }
+    };
     float hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) { hi[i][j] = 0.f; lo[i][j] = 0.f; }
+    fetch(0);
     for (int k0 = 0; k0 < n; k0 += TK) {
-        for (int e = threadIdx.x; e < TM * TK; e += 256) {
-            int r = e / TK, kk = e % TK;
-            int gr = row0 + r, gk = k0 + kk;
-            const double v = (gr < n && gk < n) ? A[(size_t)gr * n + gk] : 0.0;
-            const float h = (float)v;
-            Ah[kk][r] = h;
-            Al[kk][r] = (float)(v - (double)h);
-        }
-        for (int e = threadIdx.x; e < TK * TN; e += 256) {
-            int kk = e / TN, cc = e % TN;
-            int gk = k0 + kk, gc = col0 + cc;
-            const double v = (gk < n && gc < n) ? B[(size_t)gk * n + gc] : 0.0;
-            const float h = (float)v;
-            Bh[kk][cc] = h;
-            Bl[kk][cc] = (float)(v - (double)h);
-        }
+        stage();
         __syncthreads();
+        if (k0 + TK < n) fetch(k0 + TK);  // the next tiles' loads overlap this tile's products
 #pragma unroll 4
         for (int kk = 0; kk < TK; kk++) {
-            float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) { ah[i] = Ah[kk][ty * 4 + i]; al[i] = Al[kk][ty * 4 + i]; }
-#pragma unroll
-            for (int j = 0; j < 4; j++) { bh[j] = Bh[kk][tx * 4 + j]; bl[j] = Bl[kk][tx * 4 + j]; }
+            const float4 ah4 = *reinterpret_cast<const float4 *>(&Ah[kk][ty * 4]);
+            const float4 al4 = *reinterpret_cast<const float4 *>(&Al[kk][ty * 4]);
+            const float4 bh4 = *reinterpret_cast<const float4 *>(&Bh[kk][tx * 4]);
+            const float4 bl4 = *reinterpret_cast<const float4 *>(&Bl[kk][tx * 4]);
+            const float ah[4] = {ah4.x, ah4.y, ah4.z, ah4.w}, al[4] = {al4.x, al4.y, al4.z, al4.w};
+            const float bh[4] = {bh4.x, bh4.y, bh4.z, bh4.w}, bl[4] = {bl4.x, bl4.y, bl4.z, bl4.w};
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -706,18 +745,23 @@ constexpr int GJP_TPB = 512, GJP_WARPS = GJP_TPB / 32, GJP_BMAX = 64;
 constexpr size_t GJP_SMEM = 225 * 1024;
 
 struct GjPanelArgs {
-    double *A0, *A1;  // the matrices, n x n row-major, inverted in place
-    double *P0, *P1;  // E[:, P] of the current panel, n x bw
-    double *T0, *T1;  // its pivot rows, bw x n
+    float2 *A0, *A1;  // the matrices, n x n row-major hi/lo pairs, inverted in place
+    float2 *P0, *P1;  // E[:, P] of the current panel, n x bw
+    float2 *T0, *T1;  // its pivot rows, bw x n
     int *perm;        // [nmat][2 n]: pivot row of each column, then the inverse permutation
     int n, k0, bw;
     int *pivflag;
 };
 
-__device__ __forceinline__ float2 df2_split(double v)
+// a + b in double-float (Knuth's two-sum of the high parts, then renormalised)
+__device__ __forceinline__ float2 df2_add(float2 a, float2 b)
 {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
+    const float t = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(t, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bb)), __fsub_rn(b.x, bb));
+    const float l = __fadd_rn(err, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(t, l);
+    return make_float2(h, __fsub_rn(l, __fsub_rn(h, t)));
 }
 
 __device__ __forceinline__ double df2_join(float2 a) { return (double)a.x + (double)a.y; }
@@ -749,11 +793,6 @@ __device__ __forceinline__ float2 df2_fms(float2 s, float2 a, float2 b)
     return make_float2(h, __fsub_rn(l, __fsub_rn(h, t)));
 }
 
-__device__ __forceinline__ void gjp_best(float &v, int &r, float ov, int orr)
-{
-    if (orr >= 0 && (r < 0 || ov > v || (ov == v && orr < r))) { v = ov; r = orr; }
-}
-
 // One panel.  BW: the allocated panel width (16, 32 or 64; the last panel of a
 // matrix may use fewer columns, bw <= BW).  Lanes own columns (a lane holds
 // columns lane and lane + 32 when BW = 64; half-warps take two rows at once
@@ -768,6 +807,18 @@ __device__ __forceinline__ void gjp_best(float &v, int &r, float ov, int orr)
 // registers and updates GJP_U rows at a time, loads first, so that the
 // dependent double-float chains of several rows overlap.
 constexpr int GJP_U = 4;
+
+// Pivot candidate of row i with high part x as one ordered 32-bit key: the
+// bit pattern of |x| (non-negative floats order as unsigned integers) with its
+// low 11 bits replaced by 2047 - i, so that one warp-wide unsigned maximum
+// picks the largest |x| to 12 mantissa bits, ties to the lowest row.  Key 0:
+// no candidate (every row of a panel has a positive key).
+constexpr unsigned int GJP_ROWMASK = 2047u;
+
+__device__ __forceinline__ unsigned int gjp_key(float x, int i)
+{
+    return ((__float_as_uint(fabsf(x)) >> 11) << 11) | (GJP_ROWMASK - (unsigned int)i);
+}
 
 // 1 / a in double-float: the FP32 reciprocal y0 and one Newton step,
 // y0 + y0 (1 - a y0), the residual formed exactly by df2_fms
@@ -788,8 +839,7 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
     constexpr int RPW = 32 / TPR;               // rows per warp and pass
     constexpr int RSTEP = GJP_WARPS * RPW;      // rows per CTA and pass
     extern __shared__ float2 ps[];  // S: n BW, fcol: n, pr: GJP_BMAX; then used: n bytes
-    __shared__ float cv[GJP_WARPS];
-    __shared__ int ci[GJP_WARPS];
+    __shared__ unsigned int ck[GJP_WARPS];
     __shared__ int prow[GJP_BMAX];
     const int mat = blockIdx.x, n = a.n, k0 = a.k0, bw = a.bw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -797,9 +847,13 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
     // this thread's rows: r0, r0 + RSTEP, ...; nfull of them in whole groups of GJP_U
     const int nrow = r0 < n ? (n - r0 + RSTEP - 1) / RSTEP : 0;
     const int nfull = nrow - nrow % GJP_U;
-    double *A = mat ? a.A1 : a.A0;
-    double *Pm = mat ? a.P1 : a.P0;
-    double *Tm = mat ? a.T1 : a.T0;
+    float2 *A = mat ? a.A1 : a.A0;
+    float2 *Pm = mat ? a.P1 : a.P0;
+    float2 *Tm = mat ? a.T1 : a.T0;
+    // entry (i, c) of the panel sits at i BW + (c ^ (i mod BW)): rows stay
+    // contiguous for the row-wise phases and a column read by consecutive rows
+    // falls into distinct banks
+    auto sx = [](int i, int c) { return (size_t)i * BW + (c ^ (i & (BW - 1))); };
     int *perm = a.perm + (size_t)mat * 2 * n;
     float2 *S = ps, *fcol = ps + (size_t)n * BW, *pr = fcol + n;
     unsigned char *used = reinterpret_cast<unsigned char *>(pr + GJP_BMAX);
@@ -808,53 +862,42 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
     for (int q = tid; q < k0; q += GJP_TPB) used[perm[q]] = 1;
     // the panel into shared memory, GJP_U rows of loads in flight per thread
     for (int ib = r0; ib < n; ib += GJP_U * RSTEP) {
-        double v[GJP_U][NC];
+        float2 v[GJP_U][NC];
 #pragma unroll
         for (int u = 0; u < GJP_U; u++)
 #pragma unroll
             for (int c = 0; c < NC; c++) {
                 const int i = ib + u * RSTEP, col = cl + c * 32;
-                v[u][c] = (i < n && col < bw) ? A[(size_t)i * n + k0 + col] : 0.0;
+                v[u][c] = (i < n && col < bw) ? A[(size_t)i * n + k0 + col] : make_float2(0.f, 0.f);
             }
 #pragma unroll
         for (int u = 0; u < GJP_U; u++)
 #pragma unroll
             for (int c = 0; c < NC; c++) {
                 const int i = ib + u * RSTEP, col = cl + c * 32;
-                if (i < n) S[(size_t)i * BW + col] = df2_split(v[u][c]);
+                if (i < n) S[sx(i, col)] = v[u][c];
             }
     }
     __syncthreads();
     for (int j = 0; j < bw; j++) {
         {  // (1) column j out to fcol and zeroed; the pivot candidates
-            float v = -1.f;
-            int r = -1;
+            unsigned int key = 0;
             for (int i = tid; i < n; i += GJP_TPB) {
-                const float2 x = S[(size_t)i * BW + j];
+                const float2 x = S[sx(i, j)];
                 fcol[i] = x;
-                S[(size_t)i * BW + j] = make_float2(0.f, 0.f);
-                if (!used[i]) gjp_best(v, r, fabsf(x.x), i);
+                S[sx(i, j)] = make_float2(0.f, 0.f);
+                if (!used[i]) key = max(key, gjp_key(x.x, i));
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_down_sync(0xffffffffu, v, o);
-                const int orr = __shfl_down_sync(0xffffffffu, r, o);
-                gjp_best(v, r, ov, orr);
-            }
-            if (lane == 0) { cv[warp] = v; ci[warp] = r; }
+            key = __reduce_max_sync(0xffffffffu, key);
+            if (lane == 0) ck[warp] = key;
         }
         __syncthreads();
         if (warp == 0) {  // (2) the pivot, 1/a and the scaled pivot row
-            float v = lane < GJP_WARPS ? cv[lane] : -1.f;
-            int r = lane < GJP_WARPS ? ci[lane] : -1;
-            for (int o = GJP_WARPS / 2; o > 0; o >>= 1) {
-                const float ov = __shfl_down_sync(0xffffffffu, v, o);
-                const int orr = __shfl_down_sync(0xffffffffu, r, o);
-                gjp_best(v, r, ov, orr);
-            }
-            const int p = max(__shfl_sync(0xffffffffu, r, 0), 0);
+            const unsigned int key = __reduce_max_sync(0xffffffffu, lane < GJP_WARPS ? ck[lane] : 0u);
+            const int p = min((int)(GJP_ROWMASK - (key & GJP_ROWMASK)), n - 1);
             const float2 piv = fcol[p];
             const float2 inv = piv.x != 0.f ? df2_recip(piv) : make_float2(0.f, 0.f);
-            for (int c = lane; c < bw; c += 32) pr[c] = c == j ? inv : df2_mul(S[(size_t)p * BW + c], inv);
+            for (int c = lane; c < bw; c += 32) pr[c] = c == j ? inv : df2_mul(S[sx(p, c)], inv);
             if (lane == 0) {
                 if (piv.x == 0.f) atomicOr(a.pivflag, 1);
                 used[p] = 1;
@@ -868,36 +911,38 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
         float2 prv[NC];
 #pragma unroll
         for (int c = 0; c < NC; c++) prv[c] = cl + c * 32 < bw ? pr[cl + c * 32] : make_float2(0.f, 0.f);
-        float2 *Sc = S + (size_t)r0 * BW + cl;
-        const float2 *fc = fcol + r0;
         for (int q = 0; q < nfull; q += GJP_U) {
             float2 sv[GJP_U][NC], fv[GJP_U];
 #pragma unroll
             for (int u = 0; u < GJP_U; u++) {
-                fv[u] = fc[(size_t)(q + u) * RSTEP];
+                const int i = r0 + (q + u) * RSTEP;
+                fv[u] = fcol[i];
 #pragma unroll
-                for (int c = 0; c < NC; c++) sv[u][c] = Sc[(size_t)(q + u) * RSTEP * BW + c * 32];
+                for (int c = 0; c < NC; c++) sv[u][c] = S[sx(i, cl + c * 32)];
             }
 #pragma unroll
             for (int u = 0; u < GJP_U; u++)
 #pragma unroll
                 for (int c = 0; c < NC; c++) sv[u][c] = df2_fms(sv[u][c], fv[u], prv[c]);
 #pragma unroll
-            for (int u = 0; u < GJP_U; u++)
+            for (int u = 0; u < GJP_U; u++) {
+                const int i = r0 + (q + u) * RSTEP;
 #pragma unroll
-                for (int c = 0; c < NC; c++) Sc[(size_t)(q + u) * RSTEP * BW + c * 32] = sv[u][c];
+                for (int c = 0; c < NC; c++) S[sx(i, cl + c * 32)] = sv[u][c];
+            }
         }
         for (int q = nfull; q < nrow; q++) {
-            const float2 f = fc[(size_t)q * RSTEP];
+            const int i = r0 + q * RSTEP;
+            const float2 f = fcol[i];
 #pragma unroll
             for (int c = 0; c < NC; c++) {
-                float2 *e = Sc + (size_t)q * RSTEP * BW + c * 32;
+                float2 *e = S + sx(i, cl + c * 32);
                 *e = df2_fms(*e, f, prv[c]);
             }
         }
         if (p >= r0 && (p - r0) % RSTEP == 0)
 #pragma unroll
-            for (int c = 0; c < NC; c++) S[(size_t)p * BW + cl + c * 32] = prv[c];
+            for (int c = 0; c < NC; c++) S[sx(p, cl + c * 32)] = prv[c];
         __syncthreads();
     }
     // E[:, P] out (ld bw); the pivot rows out (panel columns: the identity), then zeroed
@@ -905,35 +950,36 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
 #pragma unroll
         for (int c = 0; c < NC; c++) {
             const int col = cl + c * 32;
-            if (col < bw) Pm[(size_t)i * bw + col] = df2_join(S[(size_t)i * BW + col]);
+            if (col < bw) Pm[(size_t)i * bw + col] = S[sx(i, col)];
         }
     for (int jr = warp; jr < bw; jr += GJP_WARPS) {
-        const double *src = A + (size_t)prow[jr] * n;
-        double *dst = Tm + (size_t)jr * n;
+        const float2 *src = A + (size_t)prow[jr] * n;
+        float2 *dst = Tm + (size_t)jr * n;
         for (int cb = lane; cb < n; cb += 8 * 32) {
-            double v[8];
+            float2 v[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const int col = cb + q * 32;
-                v[q] = col < n ? src[col] : 0.0;
+                v[q] = col < n ? src[col] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const int col = cb + q * 32, c2 = col - k0;
-                if (col < n) dst[col] = (c2 >= 0 && c2 < bw) ? (c2 == jr ? 1.0 : 0.0) : v[q];
+                if (col < n)
+                    dst[col] = (c2 >= 0 && c2 < bw) ? make_float2(c2 == jr ? 1.f : 0.f, 0.f) : v[q];
             }
         }
     }
     __syncthreads();
     for (int jr = warp; jr < bw; jr += GJP_WARPS) {
-        double *row = A + (size_t)prow[jr] * n;
-        for (int col = lane; col < n; col += 32) row[col] = 0.0;
+        float2 *row = A + (size_t)prow[jr] * n;
+        for (int col = lane; col < n; col += 32) row[col] = make_float2(0.f, 0.f);
     }
     for (int i = r0; i < n; i += RSTEP)
 #pragma unroll
         for (int c = 0; c < NC; c++) {
             const int col = cl + c * 32;
-            if (col < bw) A[(size_t)i * n + k0 + col] = 0.0;
+            if (col < bw) A[(size_t)i * n + k0 + col] = make_float2(0.f, 0.f);
         }
     if (k0 + bw == n) {  // last panel: the inverse permutation
         __syncthreads();
@@ -943,9 +989,9 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
 
 // A += Pm Tm (n x bw by bw x n) for one or two matrices (blockIdx.z), in
 // 32 x 32 tiles (many CTAs per SM: one rank-bw product is a few microseconds
-// of work): the whole bw extent of both operands is staged once as hi/lo
-// float pairs, then each thread forms 2 x 2 entries with the double-float
-// products and sums of k_dfgemm and rounds each pair once into its FP64 entry.
+// of work): the whole bw extent of both operands is staged once, then each
+// thread forms 2 x 2 entries with the double-float products and sums of
+// k_dfgemm and adds each to its entry in double-float.
 constexpr int GU_T = 32;
 
 __global__ void __launch_bounds__(256) k_gjp_update(GjPanelArgs a)
@@ -953,24 +999,22 @@ __global__ void __launch_bounds__(256) k_gjp_update(GjPanelArgs a)
     __shared__ float Ah[GJP_BMAX][GU_T + 1], Al[GJP_BMAX][GU_T + 1];
     __shared__ float Bh[GJP_BMAX][GU_T], Bl[GJP_BMAX][GU_T];
     const int n = a.n, bw = a.bw;
-    double *C = blockIdx.z ? a.A1 : a.A0;
-    const double *P = blockIdx.z ? a.P1 : a.P0;
-    const double *T = blockIdx.z ? a.T1 : a.T0;
+    float2 *C = blockIdx.z ? a.A1 : a.A0;
+    const float2 *P = blockIdx.z ? a.P1 : a.P0;
+    const float2 *T = blockIdx.z ? a.T1 : a.T0;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int row0 = blockIdx.y * GU_T, col0 = blockIdx.x * GU_T;
     for (int e = threadIdx.x; e < GU_T * bw; e += 256) {
         const int r = e / bw, kk = e - r * bw, gr = row0 + r;
-        const double v = gr < n ? P[(size_t)gr * bw + kk] : 0.0;
-        const float h = (float)v;
-        Ah[kk][r] = h;
-        Al[kk][r] = (float)(v - (double)h);
+        const float2 v = gr < n ? P[(size_t)gr * bw + kk] : make_float2(0.f, 0.f);
+        Ah[kk][r] = v.x;
+        Al[kk][r] = v.y;
     }
     for (int e = threadIdx.x; e < GU_T * bw; e += 256) {
         const int kk = e / GU_T, cc = e - kk * GU_T, gc = col0 + cc;
-        const double v = gc < n ? T[(size_t)kk * n + gc] : 0.0;
-        const float h = (float)v;
-        Bh[kk][cc] = h;
-        Bl[kk][cc] = (float)(v - (double)h);
+        const float2 v = gc < n ? T[(size_t)kk * n + gc] : make_float2(0.f, 0.f);
+        Bh[kk][cc] = v.x;
+        Bl[kk][cc] = v.y;
     }
     __syncthreads();
     float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -999,8 +1043,33 @@ __global__ void __launch_bounds__(256) k_gjp_update(GjPanelArgs a)
 #pragma unroll
         for (int j = 0; j < 2; j++) {
             const int gc = col0 + tx * 2 + j;
-            if (gc < n) C[(size_t)gr * n + gc] += (double)hi[i][j] + (double)lo[i][j];
+            if (gc < n) {
+                float2 *cp = C + (size_t)gr * n + gc;
+                *cp = df2_add(*cp, make_float2(hi[i][j], lo[i][j]));
+            }
         }
+    }
+}
+
+// FP64 matrix -> hi/lo pairs in place (each element's 8 bytes rewritten by
+// the thread that read them)
+__global__ void k_df2_split_inplace(double *x, size_t cnt)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cnt; e += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = df2_split(x[e]);
+        reinterpret_cast<float2 *>(x)[e] = v;
+    }
+}
+
+// A^-1[k][j] = S[perm[k]][pinv[j]], from the hi/lo pairs into FP64
+__global__ void k_gjp_unperm(const float2 *__restrict__ S, const int *__restrict__ perm, double *__restrict__ D,
+                             int n)
+{
+    const int *pinv = perm + n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), j = (int)(e % n);
+        D[e] = df2_join(S[(size_t)perm[k] * n + pinv[j]]);
     }
 }
 
@@ -1341,15 +1410,20 @@ static int gj_panel_invert(bfs_ctx *c, double *const *work, double *const *dst, 
         return sizeof(float2) * ((size_t)n * bwid + n + GJP_BMAX) + (size_t)n <= GJP_SMEM;
     };
     const int BW = fits(64) ? 64 : fits(32) ? 32 : fits(16) ? 16 : 0;
-    if (!BW) return 1;
+    if (!BW || n > (int)GJP_ROWMASK + 1) return 1;
     const void *fn = BW == 64 ? (const void *)k_gjp_panel<64>
                    : BW == 32 ? (const void *)k_gjp_panel<32> : (const void *)k_gjp_panel<16>;
     BFS_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJP_SMEM));
     const size_t smem = sizeof(float2) * ((size_t)n * BW + n + GJP_BMAX) + (size_t)n;
     GjPanelArgs a;
-    a.A0 = work[0];
-    a.A1 = nmat > 1 ? work[1] : work[0];
-    double *pt = c->d_gjdata;
+    // the FP64 inputs become hi/lo pairs in place (same bytes per entry)
+    for (int i = 0; i < nmat; i++) {
+        k_df2_split_inplace<<<1024, 256, 0, s>>>(work[i], (size_t)n * n);
+        c->launches++;
+    }
+    a.A0 = reinterpret_cast<float2 *>(work[0]);
+    a.A1 = reinterpret_cast<float2 *>(nmat > 1 ? work[1] : work[0]);
+    float2 *pt = reinterpret_cast<float2 *>(c->d_gjdata);
     a.P0 = pt;
     a.T0 = pt + (size_t)n * BW;
     a.P1 = nmat > 1 ? pt + 2 * (size_t)n * BW : a.P0;
@@ -1368,7 +1442,7 @@ static int gj_panel_invert(bfs_ctx *c, double *const *work, double *const *dst, 
         c->launches += 2;
     }
     for (int i = 0; i < nmat; i++) {
-        k_gj_unperm<<<1024, 256, 0, s>>>(work[i], a.perm + (size_t)i * 2 * n, dst[i], n);
+        k_gjp_unperm<<<1024, 256, 0, s>>>(reinterpret_cast<const float2 *>(work[i]), a.perm + (size_t)i * 2 * n, dst[i], n);
         c->launches++;
     }
     BFS_CUDA_TRY(c, cudaGetLastError());

@@ -53,23 +53,26 @@ __global__ void k_unpack(const double *__restrict__ u, double *__restrict__ noda
 
 // Second-order y-derivative at node (i, j); the half domain mirrors the
 // field across y = 0 (derivative 0 on that row).
-__device__ __forceinline__ double ydiff(const double *q, int N, int M, int half, double dy, int i,
+// (the FP64 pipe of this GPU is slow, so the record kernel multiplies by
+// reciprocals computed once on the host: i2dy = 1 / (2 dy))
+__device__ __forceinline__ double ydiff(const double *q, int N, int M, int half, double i2dy, int i,
                                         int j)
 {
     if (j == 0) {
         if (half) return 0.0;
-        return (-3.0 * q[i] + 4.0 * q[i + N] - q[i + 2 * N]) / (2.0 * dy);
+        return (-3.0 * q[i] + 4.0 * q[i + N] - q[i + 2 * N]) * i2dy;
     }
     if (j == M - 1)
         return (3.0 * q[i + (size_t)N * (M - 1)] - 4.0 * q[i + (size_t)N * (M - 2)] +
-                q[i + (size_t)N * (M - 3)]) / (2.0 * dy);
-    return (q[i + (size_t)N * (j + 1)] - q[i + (size_t)N * (j - 1)]) / (2.0 * dy);
+                q[i + (size_t)N * (M - 3)]) * i2dy;
+    return (q[i + (size_t)N * (j + 1)] - q[i + (size_t)N * (j - 1)]) * i2dy;
 }
 
 struct RecArgs {
     int N, M, half, Ns, Ns_cap, Nt;
     int w64, w32;  // which source-record copies to write (a residual reads one)
     double x1, y1, dx, dy, sigma, jc, ry;
+    double idx, i2dy;  // 1 / dx, 1 / (2 dy)
 };
 
 // Builds source records [0, Ns_cap) and target records [0, Nt) in FP64 and FP32.
@@ -91,22 +94,22 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
             if (!img) { i = e % N; j = e / N; }
             else { int q = e - (int)NM; i = q % N; j = 1 + q / N; }
             size_t q = (size_t)j * N + i;
-            double zy = ydiff(z, N, M, a.half, a.dy, i, j);
+            double zy = ydiff(z, N, M, a.half, a.i2dy, i, j);
             if (!img) {  // the nodal y-derivatives are also an output (bfs_unpack)
                 nodal[2 * NM + q] = zy;
-                nodal[5 * NM + q] = ydiff(ph, N, M, a.half, a.dy, i, j);
+                nodal[5 * NM + q] = ydiff(ph, N, M, a.half, a.i2dy, i, j);
             }
             double x = a.x1 + i * a.dx;
             double cx = (i == 0 || i == N - 1) ? 0.5 : 1.0;
             double cy = a.half ? ((j == M - 1) ? 0.5 : 1.0) : ((j == 0 || j == M - 1) ? 0.5 : 1.0);
             double w = a.dx * a.dy * cx * cy;
-            double w1 = w / (a.dx * a.dx), w2 = w / a.dx;
+            double w1 = w * a.idx * a.idx, w2 = w * a.idx;
             double ysg = img ? -1.0 : 1.0;
             double f = ph[q] - x, g = ps[q] - x;
             r[0] = (double)i - 0.5 * (N - 1);
             r[1] = (ysg * j - a.jc) * a.ry;
-            r[2] = z[q] / a.dx;
-            r[3] = (beta[q] + 1.0) / a.dx;
+            r[2] = z[q] * a.idx;
+            r[3] = (beta[q] + 1.0) * a.idx;
             r[4] = zx[q];
             r[5] = ysg * zy;
             r[6] = bx[q];
@@ -138,16 +141,16 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
     double xa = a.x1 + k * a.dx, xb = xa + a.dx;
     double zs = 0.5 * (z[qa] + z[qb]);
     double zxs = 0.5 * (zx[qa] + zx[qb]);
-    double zys = 0.5 * (ydiff(z, N, M, a.half, a.dy, k, l) + ydiff(z, N, M, a.half, a.dy, k + 1, l));
+    double zys = 0.5 * (ydiff(z, N, M, a.half, a.i2dy, k, l) + ydiff(z, N, M, a.half, a.i2dy, k + 1, l));
     double pxs = 0.5 * (phx[qa] + phx[qb]);
-    double pys = 0.5 * (ydiff(ph, N, M, a.half, a.dy, k, l) + ydiff(ph, N, M, a.half, a.dy, k + 1, l));
+    double pys = 0.5 * (ydiff(ph, N, M, a.half, a.i2dy, k, l) + ydiff(ph, N, M, a.half, a.i2dy, k + 1, l));
     double fs = 0.5 * ((ph[qa] - xa) + (ph[qb] - xb));
     double gs = 0.5 * ((ps[qa] - xa) + (ps[qb] - xb));
     double bs = 0.5 * (beta[qa] + beta[qb]);
     r[0] = (double)k + 0.5 - 0.5 * (N - 1);
     r[1] = ((double)l - a.jc) * a.ry;
-    r[2] = zs / a.dx;
-    r[3] = (bs + 1.0) / a.dx;
+    r[2] = zs * a.idx;
+    r[3] = (bs + 1.0) * a.idx;
     r[4] = zxs;
     r[5] = zys;
     r[6] = fs;
@@ -155,8 +158,8 @@ __global__ void k_records(double *nodal, const double *__restrict__ beta,
     r[8] = 1.0 + zxs * zxs;
     r[9] = 2.0 * zxs * zys;
     r[10] = 1.0 + zys * zys;
-    r[11] = zs / a.dx + 1.0 / a.dx;
-    r[12] = (bs + 1.0) / a.dx - 1.0 / a.dx;
+    r[11] = zs * a.idx + a.idx;
+    r[12] = (bs + 1.0) * a.idx - a.idx;
     r[13] = pxs;
     r[14] = pys;
     r[15] = (double)l - a.jc;  // row coordinate in mesh units (exact)
@@ -576,6 +579,22 @@ __device__ double antideriv_S2(double A, double B, double C, double s, double t)
     return g;
 }
 
+// One of the two logarithmic terms of antideriv_S2 at corner (s, t): which = 0
+// the t term, 1 the s term (their sum is antideriv_S2).
+__device__ double antideriv_S2_term(double A, double B, double C, double s, double t, int which)
+{
+    const double Q = A * s * s + B * s * t + C * t * t;
+    const double D = 4.0 * A * C - B * B;
+    if (which == 0) {
+        if (t == 0.0) return 0.0;
+        const double lin = 2.0 * A * s + B * t, r = 2.0 * sqrt(A * Q);
+        return t * rsqrt(A) * log((lin >= 0.0) ? lin + r : D * t * t / (r - lin));
+    }
+    if (s == 0.0) return 0.0;
+    const double lin = 2.0 * C * t + B * s, r = 2.0 * sqrt(C * Q);
+    return s * rsqrt(C) * log((lin >= 0.0) ? lin + r : D * s * s / (r - lin));
+}
+
 __device__ double rect_S2(double A, double B, double C, double s1, double s2, double t1, double t2)
 {
     return antideriv_S2(A, B, C, s2, t2) - antideriv_S2(A, B, C, s1, t2) -
@@ -610,12 +629,12 @@ __device__ __forceinline__ double zeta_yy(const double *__restrict__ z, int N, i
     return v / (dy * dy);
 }
 
-constexpr int FIN_LANES = 4;  // lanes per target in k_finish: the four corners of the closed form
-                               // (FP64 logs; more lanes leave FP64 warp slots idle)
+constexpr int FIN_LANES = 8;  // lanes per target in k_finish: one FP64 logarithm of the closed
+                               // form each (4 corners x 2 terms), a short dependent chain per lane
 
 // F2 / F7 / F1 at every half point (FIN_LANES lanes per target share the
-// split partial sums; lanes 0-3 also take the four corners of the closed-form
-// integral), radiation rows per slice.
+// split partial sums and take one logarithm each of the closed-form integral),
+// radiation rows per slice.
 __global__ void k_finish(const double *__restrict__ part, const double *__restrict__ tgt,
                          const double *__restrict__ constB, const double *__restrict__ nodal,
                          const double *__restrict__ psurf, double *__restrict__ Fu,
@@ -642,10 +661,12 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
     const double *r = tgt + (size_t)et * TREC;
     const double A = r[8], B = r[9], C = r[10];
     const double xs = a.x1 + (k + 0.5) * a.dx, ys = a.y1 + l * a.dy;
-    // corner q4 of the rectangle: (s2,t2) +, (s1,t2) -, (s2,t1) -, (s1,t1) +
-    const double sc = (q4 & 1) ? a.x1 - xs : a.xhi - xs;
-    const double tc = (q4 & 2) ? a.ylo - ys : a.yhi - ys;
-    double g2 = (is_t && q4 < 4 ? antideriv_S2(A, B, C, sc, tc) : 0.0) * (((q4 == 1) || (q4 == 2)) ? -1.0 : 1.0);
+    // lane q4: corner q4 >> 1 of the rectangle, (s2,t2) +, (s1,t2) -, (s2,t1) -, (s1,t1) +,
+    // and term q4 & 1 of its antiderivative
+    const int cq = q4 >> 1;
+    const double sc = (cq & 1) ? a.x1 - xs : a.xhi - xs;
+    const double tc = (cq & 2) ? a.ylo - ys : a.yhi - ys;
+    double g2 = (is_t ? antideriv_S2_term(A, B, C, sc, tc, q4 & 1) : 0.0) * (((cq == 1) || (cq == 2)) ? -1.0 : 1.0);
 #pragma unroll
     for (int o = 1; o < FIN_LANES; o <<= 1) {
         g2 += __shfl_xor_sync(0xffffffffu, g2, o);
@@ -741,6 +762,8 @@ static RecArgs rec_args(const bfs_ctx *c)
     a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy; a.sigma = c->opt.sign_I4;
     a.jc = c->half ? 0.0 : 0.5 * (c->M - 1);
     a.ry = c->dy / c->dx;
+    a.idx = 1.0 / c->dx;
+    a.i2dy = 1.0 / (2.0 * c->dy);
     a.w64 = a.w32 = 1;
     return a;
 }

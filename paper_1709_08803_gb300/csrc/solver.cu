@@ -277,7 +277,7 @@ struct TailBar {
     unsigned int count, gen;
 };
 
-__device__ bool tail_sync(TailBar *b, int *flag, unsigned int spin)
+__device__ bool tail_sync(TailBar *b, int *flag, unsigned int spin, unsigned int arrivals)
 {
     __shared__ int ok;
     __syncthreads();
@@ -287,7 +287,7 @@ __device__ bool tail_sync(TailBar *b, int *flag, unsigned int spin)
         const unsigned int g = *vgen;
         __threadfence();
         const unsigned int arrived = atomicAdd(&b->count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == arrivals - 1) {
             atomicExch(&b->count, 0u);
             __threadfence();
             atomicAdd(&b->gen, 1u);
@@ -317,15 +317,23 @@ struct TailArgs {
     TailBar *bar;
     int *flag;
     unsigned int spin;
+    // when Fp is set, w = (Fp - Fu) / h first (the Jv difference, 1/h in jsc[5])
+    const double *Fp, *Fu, *jsc;
 };
 
-__global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
+// One Arnoldi tail over G CTAs (this one: b) that share a.bar.
+__device__ void arnoldi_tail(const TailArgs &a, int G, int b)
 {
     __shared__ double hs[128];
     __shared__ double red[TAIL_TPB / 32];
-    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = a.n, cnt = a.cnt, m = a.m;
     const int chunk = (n + G - 1) / G, e0 = b * chunk, e1 = min(n, e0 + chunk);
+    if (a.Fp) {
+        const double ih = a.jsc[5];
+        for (int e = e0 + tid; e < e1; e += TAIL_TPB) a.w[e] = (a.Fp[e] - a.Fu[e]) * ih;
+        __syncthreads();
+    }
     double *h = a.giv + 4 * m + 1, *h2 = a.giv + 5 * m + 2;
     auto block_sum = [&](double v) {  // every thread gets the CTA total
         v = warp_sum(v);
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
             acc = warp_sum(acc);
             if (lane == 0) a.part[(size_t)i * G + b] = acc;
         }
-        if (!tail_sync(a.bar, a.flag, a.spin)) return;
+        if (!tail_sync(a.bar, a.flag, a.spin, (unsigned int)G)) return;
         // dot i reduced by CTA i (fixed order over the CTA partials)
         for (int i = b; i < cnt; i += G) {
             double v = 0.0;
@@ -356,7 +364,7 @@ __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
             v = block_sum(v);
             if (tid == 0) hp[i] = v;
         }
-        if (!tail_sync(a.bar, a.flag, a.spin)) return;
+        if (!tail_sync(a.bar, a.flag, a.spin, (unsigned int)G)) return;
         for (int i = tid; i < cnt; i += TAIL_TPB) hs[i] = __ldcg(hp + i);
         __syncthreads();
         for (int e = e0 + tid; e < e1; e += TAIL_TPB) {
@@ -371,18 +379,38 @@ __global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
     for (int e = e0 + tid; e < e1; e += TAIL_TPB) s2 = fma(a.w[e], a.w[e], s2);
     s2 = block_sum(s2);
     if (tid == 0) a.part[b] = s2;
-    if (!tail_sync(a.bar, a.flag, a.spin)) return;
+    if (!tail_sync(a.bar, a.flag, a.spin, (unsigned int)G)) return;
     if (b == 0) {
         double v = 0.0;
         for (int q = tid; q < G; q += TAIL_TPB) v += __ldcg(a.part + q);
         v = block_sum(v);
         if (tid == 0) *a.hn = sqrt(v);
     }
-    if (!tail_sync(a.bar, a.flag, a.spin)) return;
+    if (!tail_sync(a.bar, a.flag, a.spin, (unsigned int)G)) return;
     const double hn = __ldcg(a.hn);
     const double sc = hn > 0.0 ? 1.0 / hn : 0.0;
     for (int e = e0 + tid; e < e1; e += TAIL_TPB) a.Vnext[e] = a.w[e] * sc;
     if (b == 0 && tid == 0) givens_step(a.H, a.giv, m, cnt - 1, hn, a.res);
+}
+
+__global__ void __launch_bounds__(TAIL_TPB) k_arnoldi_tail(TailArgs a)
+{
+    arnoldi_tail(a, gridDim.x, blockIdx.x);
+}
+
+// The tails of several instances in one cooperative launch: CTAs
+// start[q] .. start[q+1]-1 run instance q's tail on its own barrier.
+struct MtailSet {
+    TailArgs a[GM_BMAX];
+    int start[GM_BMAX + 1];
+    int cnt;
+};
+
+__global__ void __launch_bounds__(TAIL_TPB) k_marnoldi_tail(const __grid_constant__ MtailSet s)
+{
+    int q = 0;
+    while (q + 1 < s.cnt && (int)blockIdx.x >= s.start[q + 1]) q++;
+    arnoldi_tail(s.a[q], s.start[q + 1] - s.start[q], (int)blockIdx.x - s.start[q]);
 }
 
 // g = (beta, 0, ..., 0) and V_0 scale factor
@@ -459,6 +487,40 @@ static void arnoldi_orth(bfs_ctx *c, int cnt, cudaStream_t s)
     norms_launch(c, c->d_w, n, c->d_scal + 8, nullptr, s);
 }
 
+// Device copy of the host's end-of-cycle test, for step graphs that are
+// queued before the previous step's scalars reach the host.  Scalars:
+// sc[2] GMRES target, sc[3] iteration limit, sc[7] end-of-cycle flag,
+// sc[8] |w|, sc[9] |g_{j+1}|, sc[14] Krylov iterations so far.
+__global__ void k_gm_set(double *sc, double target, double maxit)
+{
+    sc[2] = target;
+    sc[3] = maxit;
+}
+
+__global__ void k_gm_cycle(double *sc, double its)
+{
+    sc[7] = 0.0;
+    sc[14] = its;
+}
+
+// After the Arnoldi step that produced v_{j1}: count it and end the cycle on
+// convergence, a non-finite residual, an invariant subspace, a full basis or
+// the iteration limit (the tests of gm_arnoldi_host).
+__global__ void k_gm_flag(double *sc, int j1, int m)
+{
+    const double its = sc[14] + 1.0;
+    sc[14] = its;
+    const double hn = sc[8], res = sc[9];
+    const bool stop = !isfinite(res) || res <= sc[2] || hn == 0.0 || j1 >= m || its >= sc[3];
+    sc[7] = stop ? 1.0 : 0.0;
+}
+
+// Guard of a step graph: its body runs unless the previous step ended the cycle.
+__global__ void k_gm_guard(cudaGraphConditionalHandle h, const double *sc)
+{
+    cudaGraphSetConditional(h, sc[7] != 0.0 ? 0u : 1u);
+}
+
 // ---------------------------------------------------------------------------
 // GMRES as a sequence of device phases with host decisions between them.  A
 // single solve drives one instance; the batched solve drives many in lockstep
@@ -473,6 +535,8 @@ void gm_start(bfs_ctx *c, Gm &g, const double *u, const double *F, const double 
     g.target = eta * fnorm2;
     g.maxit = maxit;
     g.its = 0; g.j = 0; g.res = 0.0; g.state = Gm::BEGIN; g.status = BFS_OK;
+    k_gm_set<<<1, 1, 0, s>>>(c->d_scal, g.target, (double)maxit);
+    c->launches++;
     cudaMemsetAsync(c->d_du, 0, sizeof(double) * n, s);
     norms_launch(c, u, n, c->d_scal + 0, nullptr, s);  // |u| is fixed during the solve
     k_axpby<<<grid_for(n), 256, 0, s>>>(c->d_w, F, F, n, -1.0, 0.0, nullptr);  // r = -F
@@ -491,16 +555,25 @@ void gm_cycle_begin(bfs_ctx *c, Gm &g, double beta, cudaStream_t s)
     c->launches++;
     k_gmres_init<<<1, 1, 0, s>>>(c->d_giv, m, c->d_scal + 8);
     c->launches++;
+    k_gm_cycle<<<1, 1, 0, s>>>(c->d_scal, (double)g.its);
+    c->launches++;
     g.j = 0;
     g.state = Gm::ARNOLDI;
 }
 
 // Arnoldi step, before the residual: z = P^-1 v_j, then u + h z into d_up.
-int gm_arnoldi_pre(bfs_ctx *c, Gm &g, cudaStream_t s)
+int gm_arnoldi_sweep(bfs_ctx *c, Gm &g, cudaStream_t s)
 {
     int rc = precond_apply(c, c->d_V + (size_t)g.j * c->n, c->d_z, s);
     if (rc) return rc;
     g.precs++;
+    return BFS_OK;
+}
+
+int gm_arnoldi_pre(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    int rc = gm_arnoldi_sweep(c, g, s);
+    if (rc) return rc;
     return jv_prep(c, g.u, c->d_z, 0.0, c->opt.krylov_precision, s, true);
 }
 
@@ -519,6 +592,7 @@ int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s)
         ta.bar = reinterpret_cast<TailBar *>(c->d_tailbar);
         ta.flag = c->d_flag;
         ta.spin = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 24);
+        ta.Fp = ta.Fu = ta.jsc = nullptr;
         void *args[] = {&ta};
         BFS_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)k_arnoldi_tail, dim3(c->tail_grid),
                                                     dim3(TAIL_TPB), args, 0, s));
@@ -531,6 +605,144 @@ int gm_arnoldi_post(bfs_ctx *c, Gm &g, cudaStream_t s)
     k_givens<<<1, 1, 0, s>>>(c->d_H, c->d_giv, m, g.j, c->d_scal + 8, c->d_scal + 9);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());
+    return BFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The Arnoldi step of several instances at once (the lockstep batched solve):
+// after each instance's sweep, k_mjv_norms + k_mjv_axpy form |z|, h and
+// u + h z for all of them (the reductions and arithmetic of norms_launch,
+// k_jv_step and k_axpby); after the batched residual, k_marnoldi_tail forms
+// Jz, CGS2, v_{j+1} and the Givens step for all, each instance on a CTA group
+// of its own, sized to its unknowns.
+// ---------------------------------------------------------------------------
+struct MjvInst {
+    const double *u, *z;
+    double *up, *red, *sc;
+    int n;
+    double h_rel;
+};
+
+struct MjvSet {
+    MjvInst in[GM_BMAX];
+    int cnt;
+};
+
+__global__ void __launch_bounds__(RED_TPB) k_mjv_norms(const __grid_constant__ MjvSet s)
+{
+    __shared__ double s2[RED_TPB / 32];
+    const MjvInst &q = s.in[blockIdx.y];
+    double a = 0.0;
+    for (int i = blockIdx.x * RED_TPB + threadIdx.x; i < q.n; i += RED_BLOCKS * RED_TPB) a = fma(q.z[i], q.z[i], a);
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) s2[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double p = threadIdx.x < RED_TPB / 32 ? s2[threadIdx.x] : 0.0;
+        p = warp_sum(p);
+        if (threadIdx.x == 0) q.red[blockIdx.x] = p;
+    }
+}
+
+__global__ void __launch_bounds__(RED_BLOCKS) k_mjv_axpy(const __grid_constant__ MjvSet s)
+{
+    __shared__ double s2[RED_BLOCKS / 32];
+    __shared__ double hsh;
+    const MjvInst &q = s.in[blockIdx.y];
+    double p = q.red[threadIdx.x];
+    p = warp_sum(p);
+    if ((threadIdx.x & 31) == 0) s2[threadIdx.x >> 5] = p;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        p = threadIdx.x < RED_BLOCKS / 32 ? s2[threadIdx.x] : 0.0;
+        p = warp_sum(p);
+        if (threadIdx.x == 0) {
+            const double nz = sqrt(p), nu = q.sc[0];
+            const double h = nz > 0.0 ? q.h_rel * (1.0 + nu) / nz : 0.0;
+            hsh = h;
+            if (blockIdx.x == 0) {
+                q.sc[1] = nz;
+                q.sc[4] = h;
+                q.sc[5] = h > 0.0 ? 1.0 / h : 0.0;
+                q.sc[6] = nz > 0.0 ? 0.0 : 1.0;
+            }
+        }
+    }
+    __syncthreads();
+    const double a = 1.0, bb = 1.0 * hsh;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n; i += gridDim.x * blockDim.x)
+        q.up[i] = a * q.u[i] + bb * q.z[i];
+}
+
+int gm_multi_pre(bfs_ctx *const *cs, Gm *const *gs, int cnt, cudaStream_t s)
+{
+    for (int o = 0; o < cnt; o += GM_BMAX) {
+        MjvSet set;
+        set.cnt = std::min(GM_BMAX, cnt - o);
+        int nmax = 0;
+        for (int q = 0; q < set.cnt; q++) {
+            bfs_ctx *c = cs[o + q];
+            double h_rel = c->opt.jv_h_rel;
+            if (!(h_rel > 0.0)) h_rel = c->opt.krylov_precision == BFS_FP32C ? 3.4526698e-4 : 1.4901161193847656e-8;
+            set.in[q] = MjvInst{gs[o + q]->u, c->d_z, c->d_up, c->d_red, c->d_scal, c->n, h_rel};
+            nmax = std::max(nmax, c->n);
+        }
+        k_mjv_norms<<<dim3(RED_BLOCKS, set.cnt), RED_TPB, 0, s>>>(set);
+        k_mjv_axpy<<<dim3(std::min(grid_for(nmax), 256), set.cnt), RED_BLOCKS, 0, s>>>(set);
+        for (int q = 0; q < set.cnt; q++) cs[o + q]->launches += 2;
+        BFS_CUDA_TRY(cs[o], cudaGetLastError());
+    }
+    return BFS_OK;
+}
+
+int gm_multi_post(bfs_ctx *const *cs, Gm *const *gs, int cnt, cudaStream_t s)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_marnoldi_tail, TAIL_TPB, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    for (int o = 0; o < cnt; o += GM_BMAX) {
+        const int k = std::min(GM_BMAX, cnt - o);
+        bool multi = per_sm > 0;
+        double ntot = 0.0;
+        for (int q = 0; q < k; q++) {
+            multi = multi && cs[o + q]->tail_grid > 0 && gs[o + q]->j + 1 <= 128;
+            ntot += cs[o + q]->n;
+        }
+        if (!multi) {  // one instance at a time
+            for (int q = 0; q < k; q++) {
+                int rc = gm_arnoldi_post(cs[o + q], *gs[o + q], s);
+                if (rc) return rc;
+            }
+            continue;
+        }
+        const int sms = num_sms(cs[o]->device), cap = per_sm * sms;
+        const double target = std::min(2.0 * sms, (double)cap - k);
+        MtailSet set;
+        set.cnt = k;
+        set.start[0] = 0;
+        for (int q = 0; q < k; q++) {
+            bfs_ctx *c = cs[o + q];
+            Gm &g = *gs[o + q];
+            const int G = std::max(1, (int)(target * c->n / ntot));
+            set.start[q + 1] = set.start[q] + G;
+            TailArgs &ta = set.a[q];
+            ta.V = c->d_V; ta.w = c->d_w; ta.Vnext = c->d_V + (size_t)(g.j + 1) * c->n;
+            ta.H = c->d_H; ta.giv = c->d_giv; ta.part = c->d_red; ta.hn = c->d_scal + 8; ta.res = c->d_scal + 9;
+            ta.n = c->n; ta.cnt = g.j + 1; ta.m = c->m_alloc;
+            ta.bar = reinterpret_cast<TailBar *>(c->d_tailbar);
+            ta.flag = c->d_flag;
+            ta.spin = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 24);
+            ta.Fp = c->d_Fp; ta.Fu = g.Fbase; ta.jsc = c->d_scal;
+            g.jvs++;
+            c->launches++;
+        }
+        if (set.start[k] > cap) return BFS_ECUDA;  // cannot happen: target <= cap - k
+        void *args[] = {&set};
+        BFS_CUDA_TRY(cs[o], cudaLaunchCooperativeKernel((const void *)k_marnoldi_tail, dim3(set.start[k]),
+                                                        dim3(TAIL_TPB), args, 0, s));
+    }
     return BFS_OK;
 }
 
@@ -587,13 +799,80 @@ void gm_graphs_clear(bfs_ctx *c)
     c->gm_exec.clear();
     c->gm_nlaunch.clear();
     c->gm_nflow.clear();
+    c->gm_iscond.clear();
     c->gm_u = nullptr;
 }
 
 // The Arnoldi step of Krylov index g.j as a graph (captured on first use):
 // P^-1 v_j, u + h z, F(u + h z), J z, CGS2, v_{j+1}, Givens -- about twenty
-// kernels launched as one.  Returns null when graphs are off (profiling, or a
-// capture that failed), and the caller launches the kernels one by one.
+// kernels launched as one.  Preferred form: the step inside a conditional IF
+// node behind a one-thread guard that reads the end-of-cycle flag the
+// previous step left (k_gm_flag closes the body), so that a step can be
+// queued speculatively and does nothing if the cycle has ended.  Falls back
+// to the plain step graph if the conditional form does not instantiate, and
+// returns null when graphs are off (profiling, or a capture that failed): the
+// caller then launches the kernels one by one.
+static int capture_step(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    int rc = gm_arnoldi_pre(c, g, s);
+    if (!rc) rc = residual_launch(c, c->d_up, c->d_Fp, c->opt.krylov_precision, s);
+    if (!rc) rc = gm_arnoldi_post(c, g, s);
+    return rc;
+}
+
+static cudaGraphExec_t arnoldi_graph_cond(bfs_ctx *c, Gm &g, cudaStream_t s)
+{
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t guard = nullptr, cond = nullptr;
+    double *sc = c->d_scal;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, graph, 0, 0) == cudaSuccess;
+    if (ok) {
+        cudaKernelNodeParams kp = {};
+        void *kargs[] = {&h, &sc};
+        kp.func = (void *)k_gm_guard;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = kargs;
+        ok = cudaGraphAddKernelNode(&guard, graph, nullptr, 0, &kp) == cudaSuccess;
+    }
+    cudaGraph_t body = nullptr;
+    if (ok) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&cond, graph, &guard, nullptr, 1, &cp) == cudaSuccess;
+        if (ok) body = cp.conditional.phGraph_out[0];
+    }
+    if (ok) ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+    if (ok) {
+        c->capturing = 1;
+        int rc = capture_step(c, g, s);
+        if (!rc) {
+            k_gm_flag<<<1, 1, 0, s>>>(c->d_scal, g.j + 1, c->m_alloc);
+            c->launches++;
+        }
+        cudaGraph_t out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &out);
+        c->capturing = 0;
+        ok = !rc && e == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess;
+    if (!ok) {
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
+        c->err.clear();
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return ex;
+}
+
 static cudaGraphExec_t arnoldi_graph(bfs_ctx *c, Gm &g, cudaStream_t s, size_t &key)
 {
     if (c->prof_on || c->gm_disabled || !c->gm_warm) return nullptr;
@@ -606,68 +885,124 @@ static cudaGraphExec_t arnoldi_graph(bfs_ctx *c, Gm &g, cudaStream_t s, size_t &
         c->gm_exec.resize(key + 1, nullptr);
         c->gm_nlaunch.resize(key + 1, 0);
         c->gm_nflow.resize(key + 1, 0);
+        c->gm_iscond.resize(key + 1, 0);
     }
     if (c->gm_exec[key]) return c->gm_exec[key];
     const unsigned long long l0 = c->launches, f0 = c->flow_count;
     const int p0 = g.precs, j0 = g.jvs;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        c->gm_disabled = 1;
-        return nullptr;
+    cudaGraphExec_t ex = nullptr;
+    if (c->gm_cond >= 0) {
+        ex = arnoldi_graph_cond(c, g, s);
+        c->gm_cond = ex ? 1 : -1;
     }
-    c->capturing = 1;
-    int rc = gm_arnoldi_pre(c, g, s);
-    if (!rc) rc = residual_launch(c, c->d_up, c->d_Fp, c->opt.krylov_precision, s);
-    if (!rc) rc = gm_arnoldi_post(c, g, s);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(s, &graph);
-    c->capturing = 0;
+    const bool iscond = ex != nullptr;
+    if (!ex) {
+        c->launches = l0;
+        c->flow_count = f0;
+        g.precs = p0;
+        g.jvs = j0;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->gm_disabled = 1;
+            return nullptr;
+        }
+        c->capturing = 1;
+        int rc = capture_step(c, g, s);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        c->capturing = 0;
+        if (!rc && e == cudaSuccess && graph && cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess) {
+        } else {
+            ex = nullptr;
+            c->gm_disabled = 1;  // launch one by one from now on
+            c->err.clear();
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+    }
     const unsigned long long nl = c->launches - l0, nf = c->flow_count - f0;
     c->launches = l0;
     c->flow_count = f0;
     g.precs = p0;
     g.jvs = j0;
-    cudaGraphExec_t ex = nullptr;
-    if (!rc && e == cudaSuccess && graph && cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess) {
+    if (ex) {
         c->gm_exec[key] = ex;
         c->gm_nlaunch[key] = nl;
         c->gm_nflow[key] = nf;
-    } else {
-        ex = nullptr;
-        c->gm_disabled = 1;  // launch one by one from now on
-        c->err.clear();
+        c->gm_iscond[key] = iscond ? 1 : 0;
     }
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
     return ex;
 }
 
 // One instance: the phases above with the residual evaluated in between.
+// With conditional step graphs the loop keeps one step queued ahead: step j's
+// scalars (end-of-cycle flag, |w|, |g_{j+1}|) are copied to pinned memory
+// behind an event, step j+1 is launched, and only then does the host wait --
+// on the event, not the stream -- so the GPU never idles on the round trip.
+// A step queued past the end of a cycle finds the flag set and does nothing.
 static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s)
 {
     int rc;
-    const int kp = c->opt.krylov_precision;
+    const int kp = c->opt.krylov_precision, m = c->m_alloc;
     if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
     gm_cycle_begin(c, g, c->h_pin[0], s);
+    int queued = -1;  // Krylov index whose conditional step graph is already in the stream
+    size_t qkey = 0;
     while (g.state != Gm::DONE) {
         if (g.state == Gm::ARNOLDI) {
             size_t key = 0;
-            cudaGraphExec_t ex = arnoldi_graph(c, g, s, key);
-            if (ex) {
-                if ((rc = flow_wrap_check(c, s))) return rc;
-                BFS_CUDA_TRY(c, cudaGraphLaunch(ex, s));
+            cudaGraphExec_t ex = nullptr;
+            if (queued == g.j) {
+                key = qkey;
+                ex = c->gm_exec[key];
+            } else {
+                ex = arnoldi_graph(c, g, s, key);
+                if (ex) {
+                    if ((rc = flow_wrap_check(c, s))) return rc;
+                    BFS_CUDA_TRY(c, cudaGraphLaunch(ex, s));
+                    if (c->gm_iscond[key]) c->launches++;  // the guard
+                } else {
+                    if ((rc = gm_arnoldi_pre(c, g, s))) return rc;
+                    if ((rc = residual_launch(c, c->d_up, c->d_Fp, kp, s))) return rc;
+                    if ((rc = gm_arnoldi_post(c, g, s))) return rc;
+                    c->gm_warm = 1;
+                }
+            }
+            queued = -1;
+            if (ex) {  // the step ran: its guard saw the flag that the previous step left clear
                 c->launches += c->gm_nlaunch[key];
                 c->flow_count += c->gm_nflow[key];
                 g.precs++;
                 g.jvs++;
-            } else {
-                if ((rc = gm_arnoldi_pre(c, g, s))) return rc;
-                if ((rc = residual_launch(c, c->d_up, c->d_Fp, kp, s))) return rc;
-                if ((rc = gm_arnoldi_post(c, g, s))) return rc;
-                c->gm_warm = 1;
             }
-            if ((rc = read_scalars(c, c->d_scal + 8, 2, s))) return rc;
-            gm_arnoldi_host(c, g, c->h_pin[0], c->h_pin[1]);
+            if (ex && c->gm_iscond[key]) {
+                if (!c->gm_ev) BFS_CUDA_TRY(c, cudaEventCreateWithFlags(&c->gm_ev, cudaEventDisableTiming));
+                BFS_CUDA_TRY(c, cudaMemcpyAsync(c->h_pin + 4, c->d_scal + 7, 3 * sizeof(double),
+                                                cudaMemcpyDeviceToHost, s));
+                BFS_CUDA_TRY(c, cudaEventRecord(c->gm_ev, s));
+                if (g.j + 1 < m && g.its + 1 < g.maxit) {
+                    Gm gn = g;
+                    gn.j = g.j + 1;
+                    size_t k2 = 0;
+                    cudaGraphExec_t ex2 = arnoldi_graph(c, gn, s, k2);
+                    if (ex2 && c->gm_iscond[k2]) {
+                        if ((rc = flow_wrap_check(c, s))) return rc;
+                        BFS_CUDA_TRY(c, cudaGraphLaunch(ex2, s));
+                        c->launches++;
+                        queued = gn.j;
+                        qkey = k2;
+                    }
+                }
+                BFS_CUDA_TRY(c, cudaEventSynchronize(c->gm_ev));
+                const bool stop = c->h_pin[4] != 0.0;
+                gm_arnoldi_host(c, g, c->h_pin[5], c->h_pin[6]);
+                // the device flag decides whether the queued step ran; the tests agree
+                if (stop && g.state == Gm::ARNOLDI) g.state = Gm::CYCLE_END;
+                if (g.state != Gm::ARNOLDI) queued = -1;
+            } else {
+                if ((rc = read_scalars(c, c->d_scal + 8, 2, s))) return rc;
+                gm_arnoldi_host(c, g, c->h_pin[0], c->h_pin[1]);
+            }
         } else if (g.state == Gm::CYCLE_END) {
             if ((rc = gm_cycle_end(c, g, s))) return rc;
         } else if (g.state == Gm::RESTART) {
@@ -682,7 +1017,27 @@ static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s)
     return g.status;
 }
 
+static int solve_on(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s);
+
+// The legacy default stream cannot be captured into graphs, so a solve handed
+// it runs on the context's own non-blocking stream, ordered after the
+// caller's earlier work and before its later work by an event each way.
 int solve_device(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
+{
+    if (s != nullptr && s != cudaStreamLegacy) return solve_on(c, u, st, s);
+    if (!c->own_stream) {
+        BFS_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+        BFS_CUDA_TRY(c, cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
+    BFS_CUDA_TRY(c, cudaEventRecord(c->join_ev, s));
+    BFS_CUDA_TRY(c, cudaStreamWaitEvent(c->own_stream, c->join_ev, 0));
+    const int rc = solve_on(c, u, st, c->own_stream);
+    BFS_CUDA_TRY(c, cudaEventRecord(c->join_ev, c->own_stream));
+    BFS_CUDA_TRY(c, cudaStreamWaitEvent(s, c->join_ev, 0));
+    return rc;
+}
+
+static int solve_on(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
 {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
