@@ -312,13 +312,15 @@ int bfs_debug_stall_sweep(bfs_ctx *ctx, int task);
    method 0: FP64 Gauss-Jordan with partial pivoting, rows spread over the
    GPU, one exchange between CTAs per column (the factorisation's kernel when
    the sweeps are FP64); method 1: blocked Gauss-Jordan in double-float
-   arithmetic (panels of up to 64 columns in one CTA's shared memory, then one
-   rank-panel product per panel; the kernel when the sweeps are FP32).  Both
-   pivot on the unused row with the largest |entry|, ties to the lowest row;
-   method 1 compares the magnitudes to 12 significant bits.  Allocates its own scratch and synchronises stream.
+   arithmetic (panels of 64 columns spread over a cluster of 8 CTAs' shared
+   memory from 128 rows up, else panels of up to 64 columns in one CTA; then
+   one rank-panel product per panel; the kernel when the sweeps are FP32);
+   method 2: method 1 with one CTA per panel at every size.  All pivot on the
+   unused row with the largest |entry|, ties to the lowest row; methods 1 and
+   2 compare the magnitudes to 12 significant bits.  Allocates its own scratch and synchronises stream.
    BFS_EINVAL for a bad argument or an n the method's tiles do not take
-   (method 0: n > 16 rows per CTA; method 1: a panel of 8 columns does not
-   fit in shared memory, n > about 3500), BFS_ESINGULAR for a zero pivot,
+   (method 0: n > 16 rows per CTA; methods 1 and 2: n > 2048, or a panel of
+   16 columns does not fit in one CTA), BFS_ESINGULAR for a zero pivot,
    BFS_ETIMEOUT if a wait between CTAs gave up (method 0). */
 int bfs_gj_invert(const double *A, double *Ainv, int n, int nmat, int method, void *stream);
 

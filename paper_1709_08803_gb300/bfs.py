@@ -401,7 +401,8 @@ def peak_probe(kind: int, iters: int, out, stream=None) -> float:
 def gj_invert(A, method: int, stream=None):
     """Inverses of the (n, n) or (2, n, n) float64 CUDA tensor A by the
     factorisation's Gauss-Jordan kernels (method 0: FP64 rows kernel, 1:
-    blocked double-float); raises BfsError on a failure code."""
+    blocked double-float, clustered panels where they fit, 2: blocked
+    double-float with one CTA per panel); raises BfsError on a failure code."""
     import torch
     A = A.contiguous()
     nmat = 1 if A.dim() == 2 else A.shape[0]

@@ -37,6 +37,8 @@
 #include <memory>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "bfs_internal.cuh"
 
 namespace bfs {
@@ -987,6 +989,203 @@ __global__ void __launch_bounds__(GJP_TPB, 1) k_gjp_panel(GjPanelArgs a)
     }
 }
 
+// The same panel over a cluster of GJC_CS CTAs, rows split in contiguous
+// ranges, each range resident in its own CTA's shared memory, so that one
+// panel column costs 1/GJC_CS of the update in each CTA.  A pivot step has one
+// cluster barrier.  Before it, every CTA moves its rows' entries of column j
+// to fcol (zeroing them in S), picks its best unused row and copies that row,
+// its pivot entry and its key into a candidate slot of its own (two slots, by
+// column parity).  After it, every CTA reads the GJC_CS keys and the winner's
+// slot through distributed shared memory, forms 1/a and the scaled pivot row
+// itself (the same values in every CTA) and updates its rows.  The parity lets
+// a CTA publish column j+1 while slower ones still read column j; a final
+// cluster barrier keeps every CTA's shared memory alive until all reads end.
+constexpr int GJC_CS = 8;
+
+struct GjcSlot {
+    float2 row[GJP_BMAX];
+    float2 piv;
+    unsigned int key;
+};
+
+template <int BW>
+__global__ void __cluster_dims__(GJC_CS, 1, 1) __launch_bounds__(GJP_TPB, 1) k_gjc_panel(GjPanelArgs a)
+{
+    constexpr int TPR = BW >= 32 ? 32 : BW;
+    constexpr int NC = BW >= 32 ? BW / 32 : 1;
+    constexpr int RPW = 32 / TPR;
+    constexpr int RSTEP = GJP_WARPS * RPW;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ float2 ps[];  // S: chunk BW, fcol: chunk, pr: GJP_BMAX; then used: chunk bytes
+    __shared__ GjcSlot slot[2];
+    __shared__ unsigned int ck[GJP_WARPS];
+    __shared__ int prow[GJP_BMAX];
+    const int rank = (int)cluster.block_rank(), mat = blockIdx.x / GJC_CS;
+    const int n = a.n, k0 = a.k0, bw = a.bw;
+    const int chunk = (n + GJC_CS - 1) / GJC_CS;
+    const int rlo = min(n, rank * chunk), nr = min(n, rlo + chunk) - rlo;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cl = lane % TPR, r0 = warp * RPW + lane / TPR;
+    const int nrow = r0 < nr ? (nr - r0 + RSTEP - 1) / RSTEP : 0;
+    const int nfull = nrow - nrow % GJP_U;
+    float2 *A = mat ? a.A1 : a.A0;
+    float2 *Pm = mat ? a.P1 : a.P0;
+    float2 *Tm = mat ? a.T1 : a.T0;
+    int *perm = a.perm + (size_t)mat * 2 * n;
+    auto sx = [](int i, int c) { return (size_t)i * BW + (c ^ (i & (BW - 1))); };
+    float2 *S = ps, *fcol = ps + (size_t)chunk * BW, *pr = fcol + chunk;
+    unsigned char *used = reinterpret_cast<unsigned char *>(pr + GJP_BMAX);
+    for (int i = tid; i < nr; i += GJP_TPB) used[i] = 0;
+    __syncthreads();
+    for (int q = tid; q < k0; q += GJP_TPB) {
+        const int p = perm[q] - rlo;
+        if (p >= 0 && p < nr) used[p] = 1;
+    }
+    // this CTA's rows of the panel into shared memory
+    for (int ib = r0; ib < nr; ib += GJP_U * RSTEP) {
+        float2 v[GJP_U][NC];
+#pragma unroll
+        for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const int i = ib + u * RSTEP, col = cl + c * 32;
+                v[u][c] = (i < nr && col < bw) ? A[(size_t)(rlo + i) * n + k0 + col] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const int i = ib + u * RSTEP, col = cl + c * 32;
+                if (i < nr) S[sx(i, col)] = v[u][c];
+            }
+    }
+    __syncthreads();
+    for (int j = 0; j < bw; j++) {
+        const int par = j & 1;
+        {  // column j out to fcol and zeroed; this CTA's candidate
+            unsigned int key = 0;
+            for (int i = tid; i < nr; i += GJP_TPB) {
+                const float2 x = S[sx(i, j)];
+                fcol[i] = x;
+                S[sx(i, j)] = make_float2(0.f, 0.f);
+                if (!used[i]) key = max(key, gjp_key(x.x, rlo + i));
+            }
+            key = __reduce_max_sync(0xffffffffu, key);
+            if (lane == 0) ck[warp] = key;
+        }
+        __syncthreads();
+        if (warp == 0) {  // the candidate slot: key, pivot entry and row (column j already zeroed)
+            const unsigned int key = __reduce_max_sync(0xffffffffu, lane < GJP_WARPS ? ck[lane] : 0u);
+            GjcSlot &sl = slot[par];
+            if (key) {
+                const int li = (int)(GJP_ROWMASK - (key & GJP_ROWMASK)) - rlo;
+                for (int c = lane; c < bw; c += 32) sl.row[c] = S[sx(li, c)];
+                if (lane == 0) sl.piv = fcol[li];
+            }
+            if (lane == 0) sl.key = key;
+        }
+        cluster.sync();
+        if (warp == 0) {  // the winner over the cluster, 1/a and the scaled pivot row
+            const unsigned int rk = lane < GJC_CS ? cluster.map_shared_rank(&slot[par], lane)->key : 0u;
+            const unsigned int wkey = __reduce_max_sync(0xffffffffu, rk);
+            const int w = __ffs(__ballot_sync(0xffffffffu, lane < GJC_CS && rk == wkey)) - 1;
+            const GjcSlot *ws = cluster.map_shared_rank(&slot[par], max(w, 0));
+            const int p = min((int)(GJP_ROWMASK - (wkey & GJP_ROWMASK)), n - 1);
+            const float2 piv = ws->piv;
+            const float2 inv = piv.x != 0.f ? df2_recip(piv) : make_float2(0.f, 0.f);
+            for (int c = lane; c < bw; c += 32) pr[c] = c == j ? inv : df2_mul(ws->row[c], inv);
+            if (lane == 0) {
+                if (piv.x == 0.f && rank == 0) atomicOr(a.pivflag, 1);
+                prow[j] = p;
+                if (rank == 0) perm[k0 + j] = p;
+                if (p >= rlo && p < rlo + nr) used[p - rlo] = 1;
+            }
+        }
+        __syncthreads();
+        // every row of this CTA: S[i][c] -= f_i pr[c]; then the pivot row takes pr
+        const int pl = prow[j] - rlo;
+        float2 prv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) prv[c] = cl + c * 32 < bw ? pr[cl + c * 32] : make_float2(0.f, 0.f);
+        for (int q = 0; q < nfull; q += GJP_U) {
+            float2 sv[GJP_U][NC], fv[GJP_U];
+#pragma unroll
+            for (int u = 0; u < GJP_U; u++) {
+                const int i = r0 + (q + u) * RSTEP;
+                fv[u] = fcol[i];
+#pragma unroll
+                for (int c = 0; c < NC; c++) sv[u][c] = S[sx(i, cl + c * 32)];
+            }
+#pragma unroll
+            for (int u = 0; u < GJP_U; u++)
+#pragma unroll
+                for (int c = 0; c < NC; c++) sv[u][c] = df2_fms(sv[u][c], fv[u], prv[c]);
+#pragma unroll
+            for (int u = 0; u < GJP_U; u++) {
+                const int i = r0 + (q + u) * RSTEP;
+#pragma unroll
+                for (int c = 0; c < NC; c++) S[sx(i, cl + c * 32)] = sv[u][c];
+            }
+        }
+        for (int q = nfull; q < nrow; q++) {
+            const int i = r0 + q * RSTEP;
+            const float2 f = fcol[i];
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                float2 *e = S + sx(i, cl + c * 32);
+                *e = df2_fms(*e, f, prv[c]);
+            }
+        }
+        if (pl >= r0 && pl < nr && (pl - r0) % RSTEP == 0)
+#pragma unroll
+            for (int c = 0; c < NC; c++) S[sx(pl, cl + c * 32)] = prv[c];
+        __syncthreads();
+    }
+    cluster.sync();  // no CTA leaves while another may still read its slots
+    // E[:, P] out for this CTA's rows; the pivot rows jr = rank (mod GJC_CS) out
+    // (panel columns: the identity), then zeroed with this CTA's panel columns
+    for (int i = r0; i < nr; i += RSTEP)
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            const int col = cl + c * 32;
+            if (col < bw) Pm[(size_t)(rlo + i) * bw + col] = S[sx(i, col)];
+        }
+    for (int jr = rank + GJC_CS * warp; jr < bw; jr += GJC_CS * GJP_WARPS) {
+        const float2 *src = A + (size_t)prow[jr] * n;
+        float2 *dst = Tm + (size_t)jr * n;
+        for (int cb = lane; cb < n; cb += 8 * 32) {
+            float2 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int col = cb + q * 32;
+                v[q] = col < n ? src[col] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int col = cb + q * 32, c2 = col - k0;
+                if (col < n)
+                    dst[col] = (c2 >= 0 && c2 < bw) ? make_float2(c2 == jr ? 1.f : 0.f, 0.f) : v[q];
+            }
+        }
+    }
+    __syncthreads();
+    for (int jr = rank + GJC_CS * warp; jr < bw; jr += GJC_CS * GJP_WARPS) {
+        float2 *row = A + (size_t)prow[jr] * n;
+        for (int col = lane; col < n; col += 32) row[col] = make_float2(0.f, 0.f);
+    }
+    for (int i = r0; i < nr; i += RSTEP)
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            const int col = cl + c * 32;
+            if (col < bw) A[(size_t)(rlo + i) * n + k0 + col] = make_float2(0.f, 0.f);
+        }
+    if (k0 + bw == n && rank == 0) {  // last panel: the inverse permutation
+        __syncthreads();
+        for (int k = tid; k < n; k += GJP_TPB) perm[n + perm[k]] = k;
+    }
+}
+
 // A += Pm Tm (n x bw by bw x n) for one or two matrices (blockIdx.z), in
 // 32 x 32 tiles (many CTAs per SM: one rank-bw product is a few microseconds
 // of work): the whole bw extent of both operands is staged once, then each
@@ -1402,19 +1601,47 @@ static int gj_rows_invert(bfs_ctx *c, double *const *work, double *const *dst, i
 // if a panel of 8 columns does not fit in shared memory (the caller falls
 // back).  Scratch: the perm / pinv words after the slots of d_gjscr, Pm and Tm
 // in d_gjdata.
-static int gj_panel_invert(bfs_ctx *c, double *const *work, double *const *dst, int nmat, int n, cudaStream_t s)
+static int gj_panel_invert(bfs_ctx *c, double *const *work, double *const *dst, int nmat, int n, cudaStream_t s,
+                           bool allow_cluster = true)
 {
     // widest panel whose rows fit: BW columns of float pairs per row, plus fcol,
     // the pivot row and the used flags
     auto fits = [&](int bwid) {
         return sizeof(float2) * ((size_t)n * bwid + n + GJP_BMAX) + (size_t)n <= GJP_SMEM;
     };
-    const int BW = fits(64) ? 64 : fits(32) ? 32 : fits(16) ? 16 : 0;
+    // the cluster form (panels of 64, rows over GJC_CS CTAs) from 128 rows up,
+    // when a cluster with its shared memory can be resident
+    const int chunk = (n + GJC_CS - 1) / GJC_CS;
+    const size_t csmem = sizeof(float2) * ((size_t)chunk * 64 + chunk + GJP_BMAX) + (size_t)chunk;
+    bool clus = allow_cluster && n >= 128 && n <= (int)GJP_ROWMASK + 1 && csmem <= GJP_SMEM;
+    if (clus) {
+        clus = cudaFuncSetAttribute((const void *)k_gjc_panel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)GJP_SMEM) == cudaSuccess;
+        int ncl = 0;
+        if (clus) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(nmat * GJC_CS);
+            cfg.blockDim = dim3(GJP_TPB);
+            cfg.dynamicSmemBytes = csmem;
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = GJC_CS;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            cfg.attrs = &at;
+            cfg.numAttrs = 1;
+            clus = cudaOccupancyMaxActiveClusters(&ncl, (const void *)k_gjc_panel<64>, &cfg) == cudaSuccess &&
+                   ncl >= 1;
+        }
+        cudaGetLastError();
+    }
+    const int BW = clus ? 64 : fits(64) ? 64 : fits(32) ? 32 : fits(16) ? 16 : 0;
     if (!BW || n > (int)GJP_ROWMASK + 1) return 1;
     const void *fn = BW == 64 ? (const void *)k_gjp_panel<64>
                    : BW == 32 ? (const void *)k_gjp_panel<32> : (const void *)k_gjp_panel<16>;
-    BFS_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJP_SMEM));
-    const size_t smem = sizeof(float2) * ((size_t)n * BW + n + GJP_BMAX) + (size_t)n;
+    if (!clus)
+        BFS_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJP_SMEM));
+    const size_t smem = clus ? csmem : sizeof(float2) * ((size_t)n * BW + n + GJP_BMAX) + (size_t)n;
     GjPanelArgs a;
     // the FP64 inputs become hi/lo pairs in place (same bytes per entry)
     for (int i = 0; i < nmat; i++) {
@@ -1435,7 +1662,8 @@ static int gj_panel_invert(bfs_ctx *c, double *const *work, double *const *dst, 
     for (int k0 = 0; k0 < n; k0 += BW) {
         a.k0 = k0;
         a.bw = std::min(BW, n - k0);
-        if (BW == 64) k_gjp_panel<64><<<nmat, GJP_TPB, smem, s>>>(a);
+        if (clus) k_gjc_panel<64><<<nmat * GJC_CS, GJP_TPB, smem, s>>>(a);
+        else if (BW == 64) k_gjp_panel<64><<<nmat, GJP_TPB, smem, s>>>(a);
         else if (BW == 32) k_gjp_panel<32><<<nmat, GJP_TPB, smem, s>>>(a);
         else k_gjp_panel<16><<<nmat, GJP_TPB, smem, s>>>(a);
         k_gjp_update<<<ug, 256, 0, s>>>(a);
@@ -1731,7 +1959,7 @@ int precond_apply(bfs_ctx *c, const double *r, double *z, cudaStream_t s)
 // The Gauss-Jordan kernels on caller matrices, with scratch of its own.
 extern "C" int bfs_gj_invert(const double *A, double *Ainv, int n, int nmat, int method, void *stream)
 {
-    if (!A || !Ainv || n < 1 || n > 16384 || nmat < 1 || nmat > 2 || (method != 0 && method != 1))
+    if (!A || !Ainv || n < 1 || n > 16384 || nmat < 1 || nmat > 2 || method < 0 || method > 2)
         return BFS_EINVAL;
     std::unique_ptr<bfs_ctx> c(new bfs_ctx{});
     if (cudaGetDevice(&c->device) != cudaSuccess) return BFS_ECUDA;
@@ -1749,7 +1977,7 @@ extern "C" int bfs_gj_invert(const double *A, double *Ainv, int n, int nmat, int
         BFS_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
         BFS_CUDA_TRY(c, cudaMemcpyAsync(work, A, sizeof(double) * nmat * nn, cudaMemcpyDeviceToDevice, s));
         double *w[2] = {work, work + (nmat > 1 ? nn : 0)}, *d[2] = {Ainv, Ainv + (nmat > 1 ? nn : 0)};
-        int r = method == 1 ? bfs::gj_panel_invert(c.get(), w, d, nmat, n, s)
+        int r = method >= 1 ? bfs::gj_panel_invert(c.get(), w, d, nmat, n, s, method == 1)
                             : bfs::gj_rows_invert(c.get(), w, d, nmat, n, s);
         if (r == 1) return BFS_EINVAL;
         if (r) return r;

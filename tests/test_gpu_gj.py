@@ -1,11 +1,14 @@
 """The inversions of the block factorisation (App. B: the inverted diagonal
 blocks of the block LU and the two-ended order's middle system) on seeded
 matrices, through the C ABI: the FP64 rows kernel (method 0) and the blocked
-double-float kernels (method 1) against numpy's LU-based inverse.
+double-float kernels, with panels spread over a CTA cluster where they fit
+(method 1) and with one CTA per panel (method 2), against numpy's LU-based
+inverse.
 
-Sizes: one panel (37), the 181 x 61 slice block (546: seventeen panels of 32
-and a ragged one of 2), a wide-mesh block (1086: panels of 16, ragged 14) and
-the 181 x 61 middle system (1638: panels of 16, ragged 6).  The matrices are
+Sizes: one panel (37), the 181 x 61 slice block (546: method 1 eight panels
+of 64 and a ragged one of 34 over eight CTAs; method 2 seventeen panels of 32
+and a ragged one of 2), a wide-mesh block (1086) and the 181 x 61 middle
+system (1638: method 2 panels of 16, ragged 6).  The matrices are
 I + 0.5 G / sqrt(n) (G standard normal, condition number near 10) with their
 rows shuffled, so that no diagonal entry is a usable pivot and partial
 pivoting decides every column.
@@ -36,10 +39,10 @@ def _matrix(n, seed):
     return B[rng.permutation(n)]
 
 
-BARS = {0: 1e-12, 1: 3e-12}
+BARS = {0: 1e-12, 1: 3e-12, 2: 3e-12}
 
 
-@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("method", [0, 1, 2])
 @pytest.mark.parametrize("n", [1, 37, 546, 1086, 1638])
 def test_inverse_matches_numpy(n, method):
     from paper_1709_08803_gb300 import bfs
@@ -51,7 +54,7 @@ def test_inverse_matches_numpy(n, method):
     assert err <= BARS[method], err
 
 
-@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("method", [0, 1, 2])
 def test_two_matrices_at_once(method):
     """The factorisation inverts the diagonal blocks of the two chains in one
     launch; each matrix gets its own pivots."""
@@ -64,10 +67,11 @@ def test_two_matrices_at_once(method):
         assert np.abs(X[q] - ref).max() / np.abs(ref).max() <= BARS[method]
 
 
-@pytest.mark.parametrize("method", [0, 1])
-def test_zero_column_is_singular(method):
+@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("n", [100, 300])
+def test_zero_column_is_singular(method, n):
     from paper_1709_08803_gb300 import bfs
-    A = _matrix(100, 3)
+    A = _matrix(n, 3)
     A[:, 61] = 0.0
     with pytest.raises(bfs.BfsError) as e:
         bfs.gj_invert(torch.tensor(A, device="cuda"), method)
