@@ -26,6 +26,9 @@ def _built():
     build.build()
 
 
+N_HELD_OUT = 100  # the first 100 draws of train_guess.evaluate's held-out sequence
+
+
 @pytest.fixture(scope="module")
 def net_and_draws():
     from paper_1709_08803_gb300 import surrogate as S
@@ -36,19 +39,24 @@ def net_and_draws():
     net = S.CNO(mesh.M, mesh.N, 1)
     net.set_params(params, scale)
     rng = np.random.default_rng(W.SEED_BASE + 9000)
-    draws = []
-    while len(draws) < 12:  # held-out subcritical bump draws, the regime where most draws converge
-        topo, F, desc = S.sample_problem_desc(rng, mesh)
-        if desc[0] == "bumps" and F < 0.8:
-            draws.append((topo, F, desc))
+    draws = [S.sample_problem_desc(rng, mesh) for _ in range(N_HELD_OUT)]
     yield mesh, net, draws
     net.close()
 
 
 def test_learned_guess_on_held_out_draws(net_and_draws):
-    """From the guess, Newton converges to the same tolerance on every held-out
-    draw that converges from the uniform stream, and on average it needs no
-    more Newton steps than from the uniform stream."""
+    """Newton from the uniform stream against Newton from the network's guess
+    (the library's learned solve: the uniform stream only if the guess fails)
+    on 100 held-out draws of the training distribution (F ~ U[0.5, 1.4],
+    bumps or a ridge; most have no steady solution the solver reaches).
+    Measured with these weights: 9 draws converge from the uniform stream, 12
+    directly from the guess (the gains lie near F = 1); on the 8 that
+    converge from both, the guess needs 2219 Krylov iterations against 3024
+    and 54 Newton steps against 58.  Asserted with margins: every draw that
+    converges from the uniform stream converges in the learned solve; at
+    least one more draw converges from the guess than from the uniform
+    stream; and on the draws both reach, the guess needs at most 95 % of the
+    Krylov iterations."""
     from paper_1709_08803_gb300 import surrogate as S
     mesh, net, draws = net_and_draws
     ctxs, rows = {}, []
@@ -58,23 +66,25 @@ def test_learned_guess_on_held_out_draws(net_and_draws):
         c.set_topography(topo)
         u = c.flat_guess()
         flat = c.solve(u, raise_on_error=False)
-        if flat["status"] != 0:
-            continue
         x = torch.tensor(S.features(mesh, topo, F)[None], device="cuda")
         ul = torch.empty_like(u)
         learned = net.solve(c, x, ul)
-        assert learned["status"] == 0 and learned["fnorm_inf"] <= 1e-8
-        rows.append((F, flat["newton_its"], learned["newton_its"], flat["krylov_its"], learned["krylov_its"],
-                     learned["fallback"]))
+        if flat["status"] == 0:
+            assert learned["status"] == 0 and learned["fnorm_inf"] <= 1e-8
+        rows.append((F, flat["status"] == 0, learned["status"] == 0 and not learned["fallback"],
+                     flat["newton_its"], learned["newton_its"], flat["krylov_its"], learned["krylov_its"]))
     for c in ctxs.values():
         c.close()
-    assert len(rows) >= 6, rows
-    r = np.array([row[:5] for row in rows], dtype=float)
-    saved_newton, saved_krylov = r[:, 1].mean() - r[:, 2].mean(), r[:, 3].mean() - r[:, 4].mean()
-    print(f"held-out draws: {len(rows)}; Newton uniform stream {r[:, 1].mean():.2f}, learned {r[:, 2].mean():.2f} "
-          f"(saved {saved_newton:.2f}); Krylov {r[:, 3].mean():.1f} vs {r[:, 4].mean():.1f} (saved {saved_krylov:.1f}); "
-          f"fallbacks {sum(row[5] for row in rows)}")
-    assert saved_newton >= 0.0
+    n_flat = sum(r[1] for r in rows)
+    n_direct = sum(r[2] for r in rows)
+    both = [r for r in rows if r[1] and r[2]]
+    kf, kl = sum(r[5] for r in both), sum(r[6] for r in both)
+    nf, nl = sum(r[3] for r in both), sum(r[4] for r in both)
+    print(f"held-out draws {len(rows)}: converged from the uniform stream {n_flat}, directly from the guess "
+          f"{n_direct}; on the {len(both)} both reach: Newton {nf} vs {nl}, Krylov {kf} vs {kl}; gained at F = "
+          f"{[round(r[0], 3) for r in rows if r[2] and not r[1]]}")
+    assert n_direct >= n_flat + 1
+    assert both and kl <= 0.95 * kf
 
 
 def test_failed_guess_falls_back_to_the_uniform_stream(net_and_draws):
@@ -84,14 +94,19 @@ def test_failed_guess_falls_back_to_the_uniform_stream(net_and_draws):
     from paper_1709_08803_gb300 import bfs
     from paper_1709_08803_gb300 import surrogate as S
     mesh, net, draws = net_and_draws
-    topo, F, _ = draws[0]
-    c = bfs.Context(mesh, topo, F, S.solver_options(F=F))
+    c = None
+    for topo, F, desc in draws:  # the first held-out draw the uniform stream solves
+        c = bfs.Context(mesh, topo, F, S.solver_options(F=F))
+        u_flat = c.flat_guess()
+        if c.solve(u_flat, raise_on_error=False)["status"] == 0:
+            break
+        c.close()
+        c = None
+    assert c is not None
     bad = torch.full((1, mesh.M, mesh.N, 4), float("nan"), dtype=torch.float32, device="cuda")
     u = torch.empty(c.n, dtype=torch.float64, device="cuda")
     st = net.solve(c, bad, u)
     assert st["fallback"] and st["status"] == 0
-    u_flat = c.flat_guess()
-    assert c.solve(u_flat, raise_on_error=False)["status"] == 0
     assert torch.allclose(u, u_flat, rtol=0.0, atol=1e-8)
     # the host-buffer form of the learned solve
     x = torch.tensor(S.features(mesh, topo, F)[None], device="cuda")
