@@ -309,6 +309,43 @@ def run_apply(args):
     return 0
 
 
+def run_factor(args):
+    """The preconditioner factorisation alone at 181 x 61 (or 361 x 121 with
+    --config large) in the mixed form's arithmetic (double-float products and
+    inversions for the FP32 sweeps, --precond fp64 for the FP64 one): what a
+    new (mesh, F) pays once before its first solve.  Wall time of
+    bfs_precond_factor, which synchronises (host table build included)."""
+    import torch
+
+    import __graft_entry__
+    from paper_1709_08803_gb300 import bfs
+    from paper_1709_08803_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    __graft_entry__.build()
+    if args.config == "large":
+        mesh, topo, F = W.config_large()
+    else:
+        mesh, topo, F = W.config_paper_scale(args.F)
+    ctx = bfs.Context(mesh, topo, F, bfs.default_options(precond_precision=_pc_prec(args)))
+    for _ in range(args.warmup):
+        ctx.precond_factor()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctx.precond_factor()
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t0) * 1e3)
+    pinfo = ctx.precond_info()
+    print(json.dumps({"mode": "factor", "metric": f"preconditioner factorisation at {mesh.N}x{mesh.M}",
+                      "unit": "ms", "value": min(times), "mean_ms": sum(times) / len(times), "steps": args.steps,
+                      "warmup": args.warmup, "half_band": pinfo["half_band"], "twist": pinfo["twist"],
+                      "precond": args.precond, "slice_block": 3 * (mesh.N + 1)}))
+    ctx.close()
+    return 0
+
+
 def batch_summary(args, steps: int, warmup: int) -> dict:
     """Batched sweep: args.batch instances (F ~ U[0.5, 1.4], 1-3 Gaussians or a
     ridge, meshes 61x21 ... 241x81) solved in lockstep; one step = one batched
@@ -417,9 +454,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep key")
     ap.add_argument("--no-learned", action="store_true",
                     help="time the solve from the uniform stream even when trained weights exist")
-    ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch", "apply"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "residual", "batch", "apply", "factor"],
                     help="solve: the JFNK step; residual: residual evaluations only; "
-                         "batch: the 64-instance batched sweep")
+                         "batch: the 64-instance batched sweep; apply: preconditioner sweeps only; "
+                         "factor: the preconditioner factorisation only")
     ap.add_argument("--batch", type=int, default=64, help="instances in --mode batch")
     ap.add_argument("--config", default="paper", choices=["paper", "large"],
                     help="--mode residual: 181x61 (paper) or 361x121 (large)")
@@ -428,6 +466,8 @@ def main():
         return run_reference(args)
     if args.mode == "residual":
         return run_residual(args)
+    if args.mode == "factor":
+        return run_factor(args)
     if args.mode == "apply":
         return run_apply(args)
     if args.mode == "batch":
