@@ -233,13 +233,14 @@ def compare_bump_pressure(eps: float = 0.285, half_band: int = 3, tol: float = 1
     return rep
 
 
-def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max_newton: int = 40):
+def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max_newton: int = 25):
     """The large configuration (361 x 121, dx = dy = 0.2, F = 0.9, bump 0.3 plus
     a cross-stream ridge; 7.6e9 pair evaluations per residual): the mixed form
     from the uniform stream and from the guess network's output (accepted only
     through Newton, the uniform stream as fallback), and the plain FP64 form
-    from the uniform stream.  Reports each solve's counts and time, and how far
-    the mixed solutions lie from the FP64 one."""
+    from the same start (by continuation in bump height, 1/3, 2/3, 1, when the
+    direct solve from the uniform stream fails).  Reports each solve's counts
+    and time, and how far the mixed solution lies from the FP64 one."""
     import torch
 
     from . import bfs
@@ -272,6 +273,16 @@ def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max
         return u
 
     u_flat = solve(ctx, ctx.flat_guess(), "mixed_uniform_stream")
+    route = "direct"
+    if rep["solves"]["mixed_uniform_stream"]["status"] != 0:
+        # the method without the network, as the paper reaches large
+        # amplitudes: continuation in bump height, each stage from the last
+        t = time.perf_counter()
+        u_flat, status, cost = S.solve_with_continuation(ctx, topo, direct_first=False)
+        rep["solves"]["mixed_continuation"] = {"status": status, **cost, "seconds": time.perf_counter() - t}
+        log(json.dumps({"mixed_continuation": rep["solves"]["mixed_continuation"]}))
+        route = "continuation"
+    ctx.set_topography(topo)
     if with_learned:
         import os
         if os.path.exists(S.WEIGHTS):
@@ -299,7 +310,14 @@ def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max
         ctx64.precond_factor()
         torch.cuda.synchronize()
         rep["factor_s_fp64"] = time.perf_counter() - t0
-        u64 = solve(ctx64, ctx64.flat_guess(), "plain_fp64")
+        if route == "direct":
+            u64 = solve(ctx64, ctx64.flat_guess(), "plain_fp64")
+        else:
+            t = time.perf_counter()
+            u64, status, cost = S.solve_with_continuation(ctx64, topo, direct_first=False)
+            rep["solves"]["plain_fp64_continuation"] = {"status": status, **cost,
+                                                         "seconds": time.perf_counter() - t}
+            log(json.dumps({"plain_fp64_continuation": rep["solves"]["plain_fp64_continuation"]}))
         z64 = ctx64.unpack(u64)["zeta"]
         rep["max_abs_zeta_mixed_minus_fp64"] = float((z - z64).abs().max())
         ctx64.close()
