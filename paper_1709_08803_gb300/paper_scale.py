@@ -233,7 +233,8 @@ def compare_bump_pressure(eps: float = 0.285, half_band: int = 3, tol: float = 1
     return rep
 
 
-def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max_newton: int = 25):
+def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max_newton: int = 25,
+              max_krylov: int = 400):
     """The large configuration (361 x 121, dx = dy = 0.2, F = 0.9, bump 0.3 plus
     a cross-stream ridge; 7.6e9 pair evaluations per residual): the mixed form
     from the uniform stream and from the guess network's output (accepted only
@@ -249,9 +250,9 @@ def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max
 
     mesh, topo, F = W.config_large()
     mixed = bfs.default_options(tol=1e-8, krylov_precision=bfs.BFS_FP32C, outer_precision=bfs.BFS_DF64,
-                                eta=1e-2, forcing=1, max_newton=max_newton, max_krylov=400,
+                                eta=1e-2, forcing=1, max_newton=max_newton, max_krylov=max_krylov,
                                 refine_below=1e-5, precond_precision=bfs.BFS_FP32C)
-    rep = {"case": "large", "mesh": "361x121", "F": F, "unknowns": mesh.n_unknowns,
+    rep = {"case": "large", "mesh": "361x121", "F": F, "unknowns": mesh.n_unknowns, "max_krylov": max_krylov,
            "pair_evals_per_residual": mesh.pair_evals(), "solves": {}}
     ctx = bfs.Context(mesh, topo, F, mixed)
     t0 = time.perf_counter()
@@ -340,6 +341,7 @@ def main(argv=None):
     ap.add_argument("--save-u", default=None, help="unknown vector of the last converged stage (.npz)")
     ap.add_argument("--start-u", default=None, help="start from a --save-u file instead of the uniform stream")
     ap.add_argument("--no-secant", action="store_true", help="start each stage from the previous solution only")
+    ap.add_argument("--no-plain", action="store_true", help="large case: skip the plain FP64 solve")
     ap.add_argument("--out", default=None, help="report (JSON), rewritten after every stage")
     ap.add_argument("--fields", default=None, help="surface fields of every converged stage (.npz)")
     ap.add_argument("--analyse", default=None,
@@ -357,7 +359,8 @@ def main(argv=None):
     __graft_entry__.build()
     saved = {}
     if a.case == "large":
-        rep = run_large(log=lambda m: print(m, file=sys.stderr, flush=True), max_newton=a.max_newton)
+        rep = run_large(log=lambda m: print(m, file=sys.stderr, flush=True), max_newton=a.max_newton,
+                        max_krylov=a.max_krylov, with_plain=not a.no_plain)
         if a.out:
             with open(a.out, "w") as fh:
                 json.dump(rep, fh, indent=1)
