@@ -595,25 +595,6 @@ __device__ double antideriv_S2_term(double A, double B, double C, double s, doub
     return s * rsqrt(C) * log((lin >= 0.0) ? lin + r : D * s * s / (r - lin));
 }
 
-// The same term in FP32, for the FP32C residual.  The form is well
-// conditioned (D = 4 (1 + zx^2 + zy^2) >= 4, Q > 0, and r - lin adds two
-// non-negative numbers), so each term carries a few FP32 roundings; the eight
-// terms are summed in FP64 and enter F2 scaled by the local slope, far below
-// the FP32 rounding of the pair sums beside them.
-__device__ float antideriv_S2_term_f(float A, float B, float C, float s, float t, int which)
-{
-    const float Q = A * s * s + B * s * t + C * t * t;
-    const float D = 4.0f * A * C - B * B;
-    if (which == 0) {
-        if (t == 0.0f) return 0.0f;
-        const float lin = 2.0f * A * s + B * t, r = 2.0f * sqrtf(A * Q);
-        return t * rsqrtf(A) * logf((lin >= 0.0f) ? lin + r : D * t * t / (r - lin));
-    }
-    if (s == 0.0f) return 0.0f;
-    const float lin = 2.0f * C * t + B * s, r = 2.0f * sqrtf(C * Q);
-    return s * rsqrtf(C) * logf((lin >= 0.0f) ? lin + r : D * s * s / (r - lin));
-}
-
 __device__ double rect_S2(double A, double B, double C, double s1, double s2, double t1, double t2)
 {
     return antideriv_S2(A, B, C, s2, t2) - antideriv_S2(A, B, C, s1, t2) -
@@ -655,7 +636,6 @@ constexpr int FIN_LANES = 8;  // lanes per target in k_finish: one FP64 logarith
 // F2 / F7 / F1 at every half point (FIN_LANES lanes per target share the
 // split partial sums and take one logarithm each of the closed-form integral),
 // radiation rows per slice.
-template <bool F32>
 __global__ void k_finish(const double *__restrict__ part, const double *__restrict__ tgt,
                          const double *__restrict__ constB, const double *__restrict__ nodal,
                          const double *__restrict__ psurf, double *__restrict__ Fu,
@@ -687,10 +667,7 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
     const int cq = q4 >> 1;
     const double sc = (cq & 1) ? a.x1 - xs : a.xhi - xs;
     const double tc = (cq & 2) ? a.ylo - ys : a.yhi - ys;
-    double g2 = 0.0;
-    if (is_t)
-        g2 = F32 ? (double)antideriv_S2_term_f((float)A, (float)B, (float)C, (float)sc, (float)tc, q4 & 1)
-                 : antideriv_S2_term(A, B, C, sc, tc, q4 & 1);
+    double g2 = is_t ? antideriv_S2_term(A, B, C, sc, tc, q4 & 1) : 0.0;
     if ((cq == 1) || (cq == 2)) g2 = -g2;
 #pragma unroll
     for (int o = 1; o < FIN_LANES; o <<= 1) {
@@ -871,12 +848,8 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
     if (ev1) cudaEventRecord(ev1, s);
     FinArgs fa = fin_args(c, p.splits);
     int tot = FIN_LANES * (c->Nt + c->M);
-    if (precision == BFS_FP32C)
-        k_finish<true><<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf,
-                                                         Fu, c->d_flag, fa);
-    else
-        k_finish<false><<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf,
-                                                          Fu, c->d_flag, fa);
+    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
+                                               c->d_flag, fa);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());
     return BFS_OK;
@@ -887,12 +860,8 @@ int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s)
     const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
     FinArgs fa = fin_args(c, p.splits);
     int tot = FIN_LANES * (c->Nt + c->M);
-    if (precision == BFS_FP32C)
-        k_finish<true><<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf,
-                                                         Fu, c->d_flag, fa);
-    else
-        k_finish<false><<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf,
-                                                          Fu, c->d_flag, fa);
+    k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
+                                               c->d_flag, fa);
     c->launches++;
     BFS_CUDA_TRY(c, cudaGetLastError());
     return BFS_OK;
