@@ -38,7 +38,7 @@ FP32_OPS_PER_INDEX_PAIR = 45
 MUFU_PER_INDEX_PAIR = 5  # reciprocal square roots per (target, source) index pair
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP32C pair-kernel launch at
 # 181x61 from an ncu capture of the current kernel
-PAIRS_TRAFFIC = 1.431808e6  # profiles/k_pairs_181x61.md
+PAIRS_TRAFFIC = 1.4336e6  # profiles/k_pairs_181x61.md (43 x 87 CTAs)
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP32 sweep launch at
 # 181x61 from an ncu capture of the current kernel; None until captured
 APPLY_TRAFFIC = 500.9e6  # profiles/k_apply_sweep_181x61.md

@@ -166,6 +166,17 @@ int bfs_setup(const bfs_mesh *mesh, const bfs_topo *topo, double F, const bfs_op
     cudaGetDevice(&c->device);
     const int sms = bfs::num_sms(c->device);
     bfs::plans_for(c->Nt, c->Ns, o.src_splits, sms, &c->plan64, &c->plan32);
+    if (o.src_splits <= 0) {
+        // FP32C: down to one chunk of sources per split while the split partial
+        // sums stay below 2^20 target slots (40 MB): many short CTAs, so that the
+        // last wave of the launch is a small part of it (the split count changes
+        // only how the chunk totals are grouped: a two-sum within a split, FP64
+        // across splits; the 181 x 61 residuals came out identical)
+        const int nchunks = (c->Ns + c->plan32.chunk - 1) / c->plan32.chunk;
+        const int fine = std::min(nchunks, std::max(c->plan32.splits, (1 << 20) / std::max(c->Nt, 1)));
+        if (fine > c->plan32.splits)
+            c->plan32 = bfs::make_plan(c->Nt, c->Ns, c->plan32.tpb, c->plan32.tpt, c->plan32.chunk, fine, sms);
+    }
     c->plandf = bfs::plan_df(c->Nt, c->Ns, o.src_splits, sms);
     c->Ns_cap = std::max(c->plan64.splits * c->plan64.per_split, c->plan32.splits * c->plan32.per_split);
     c->Ns_cap = std::max(c->Ns_cap, c->plandf.splits * c->plandf.per_split);
