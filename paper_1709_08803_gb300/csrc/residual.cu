@@ -526,12 +526,14 @@ __device__ __forceinline__ void pair_tile_x2(const float *__restrict__ src, int 
         __syncthreads();  // every thread is done with this buffer before it is refilled
     }
     ring.seq = q0 + nch;
+    // the split's sums as hi/lo float pairs (8 bytes, like the FP64 partials of the
+    // other kernels): k_finish adds them in double-float on the FP32 pipes
+    float2 *pf = reinterpret_cast<float2 *>(part);
 #pragma unroll
     for (int p = 0; p < TPT; p++) {
         if (tid[p] >= Nt) continue;
 #pragma unroll
-        for (int q = 0; q < NACC; q++)
-            part[((size_t)split * NACC + q) * Nt + tid[p]] = (double)hi[p][q] + (double)lo[p][q];
+        for (int q = 0; q < NACC; q++) pf[((size_t)split * NACC + q) * Nt + tid[p]] = make_float2(hi[p][q], lo[p][q]);
     }
 }
 
@@ -603,6 +605,7 @@ __device__ double rect_S2(double A, double B, double C, double s1, double s2, do
 
 struct FinArgs {
     int N, M, Nt, splits, half;
+    int part_f2;  // the partials are hi/lo float pairs (FP32C pair kernels), not FP64
     double x1, y1, dx, dy, ylo, yhi, xhi, F, n_rad, tau;
     double iF2;  // 1 / F^2 (the FP64 pipe of this GPU is slow: no division per target)
 };
@@ -633,6 +636,18 @@ __device__ __forceinline__ double zeta_yy(const double *__restrict__ z, int N, i
 constexpr int FIN_LANES = 8;  // lanes per target in k_finish: one FP64 logarithm of the closed
                                // form each (4 corners x 2 terms), a short dependent chain per lane
 
+// a + b in double-float: Knuth's two-sum of the high parts, the low parts added,
+// renormalised (the explicit _rn operations keep the compiler from contracting)
+__device__ __forceinline__ float2 fin_df_add(float2 a, float2 b)
+{
+    const float t = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(t, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bb)), __fsub_rn(b.x, bb));
+    const float l = __fadd_rn(err, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(t, l);
+    return make_float2(h, __fsub_rn(l, __fsub_rn(h, t)));
+}
+
 // F2 / F7 / F1 at every half point (FIN_LANES lanes per target share the
 // split partial sums and take one logarithm each of the closed-form integral),
 // radiation rows per slice.
@@ -652,7 +667,32 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
     double acc[NACC];
 #pragma unroll
     for (int q = 0; q < NACC; q++) acc[q] = 0.0;
-    if (is_t) {
+    if (a.part_f2) {
+        // hi/lo pairs summed in double-float (Knuth's two-sum on the FP32 pipes; an
+        // FP64 addition costs this GPU the pipe time of 64 FP32 ones), lanes joined
+        // by an xor tree, then one FP64 rounding
+        const float2 *pf = reinterpret_cast<const float2 *>(part);
+        float2 d[NACC];
+#pragma unroll
+        for (int q = 0; q < NACC; q++) d[q] = make_float2(0.f, 0.f);
+        if (is_t) {
+#pragma unroll 2
+            for (int s = q4; s < a.splits; s += FIN_LANES)
+#pragma unroll
+                for (int q = 0; q < NACC; q++) d[q] = fin_df_add(d[q], pf[((size_t)s * NACC + q) * a.Nt + et]);
+        }
+#pragma unroll
+        for (int o = 1; o < FIN_LANES; o <<= 1)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) {
+                const float2 od = make_float2(__shfl_xor_sync(0xffffffffu, d[q].x, o),
+                                              __shfl_xor_sync(0xffffffffu, d[q].y, o));
+                d[q] = fin_df_add(d[q], od);
+            }
+        if (q4 == 0)
+#pragma unroll
+            for (int q = 0; q < NACC; q++) acc[q] = (double)d[q].x + (double)d[q].y;
+    } else if (is_t) {
 #pragma unroll 2
         for (int s = q4; s < a.splits; s += FIN_LANES)
 #pragma unroll
@@ -672,8 +712,9 @@ __global__ void k_finish(const double *__restrict__ part, const double *__restri
 #pragma unroll
     for (int o = 1; o < FIN_LANES; o <<= 1) {
         g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+        if (!a.part_f2)
 #pragma unroll
-        for (int q = 0; q < NACC; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            for (int q = 0; q < NACC; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     }
     if (is_t && q4 == 0) {
         const double zs = r[2] * a.dx, zxs = r[4], zys = r[5], fs = r[6], gs = r[7];
@@ -770,10 +811,11 @@ static RecArgs rec_args(const bfs_ctx *c)
     return a;
 }
 
-static FinArgs fin_args(const bfs_ctx *c, int splits)
+static FinArgs fin_args(const bfs_ctx *c, int splits, int part_f2 = 0)
 {
     FinArgs a;
     a.N = c->N; a.M = c->M; a.Nt = c->Nt; a.splits = splits; a.half = c->half;
+    a.part_f2 = part_f2;
     a.tau = c->opt.surface_tension;
     a.x1 = c->x1; a.y1 = c->y1; a.dx = c->dx; a.dy = c->dy;
     a.iF2 = 1.0 / (c->F * c->F);
@@ -846,7 +888,7 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
             <<<grid, P64_TPB, 0, s>>>(c->d_src64, p.per_split, c->d_tgt64, c->Nt, c->d_part, c->d_flag);
     if (precision != BFS_DF64) c->launches++;
     if (ev1) cudaEventRecord(ev1, s);
-    FinArgs fa = fin_args(c, p.splits);
+    FinArgs fa = fin_args(c, p.splits, precision == BFS_FP32C);
     int tot = FIN_LANES * (c->Nt + c->M);
     k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
                                                c->d_flag, fa);
@@ -858,7 +900,7 @@ int residual_launch(bfs_ctx *c, const double *u, double *Fu, int precision, cuda
 int finish_launch(bfs_ctx *c, double *Fu, int precision, cudaStream_t s)
 {
     const PairPlan &p = precision == BFS_FP32C ? c->plan32 : (precision == BFS_DF64 ? c->plandf : c->plan64);
-    FinArgs fa = fin_args(c, p.splits);
+    FinArgs fa = fin_args(c, p.splits, precision == BFS_FP32C);
     int tot = FIN_LANES * (c->Nt + c->M);
     k_finish<<<(tot + 127) / 128, 128, 0, s>>>(c->d_part, c->d_tgt64, c->d_constB, c->d_nodal, c->d_psurf, Fu,
                                                c->d_flag, fa);
