@@ -940,12 +940,18 @@ static cudaGraphExec_t arnoldi_graph(bfs_ctx *c, Gm &g, cudaStream_t s, size_t &
 // behind an event, step j+1 is launched, and only then does the host wait --
 // on the event, not the stream -- so the GPU never idles on the round trip.
 // A step queued past the end of a cycle finds the flag set and does nothing.
-static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s)
+static int gmres(bfs_ctx *c, Gm &g, cudaStream_t s, double beta_known)
 {
     int rc;
     const int kp = c->opt.krylov_precision, m = c->m_alloc;
-    if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
-    gm_cycle_begin(c, g, c->h_pin[0], s);
+    // |r| of the first cycle is |F|_2, which the caller already holds bit for
+    // bit (the same norm kernel on -F): no round trip for it
+    if (beta_known >= 0.0) {
+        gm_cycle_begin(c, g, beta_known, s);
+    } else {
+        if ((rc = read_scalars(c, c->d_scal + 8, 1, s))) return rc;
+        gm_cycle_begin(c, g, c->h_pin[0], s);
+    }
     int queued = -1;  // Krylov index whose conditional step graph is already in the stream
     size_t qkey = 0;
     while (g.state != Gm::DONE) {
@@ -1120,7 +1126,7 @@ static int solve_on(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
         gk.precs = g.precs;
         gk.jvs = g.jvs;
         gm_start(c, gk, u, c->d_F, Fbase, f2, eta_k, c->opt.max_krylov, s);
-        rc = gmres(c, gk, s);
+        rc = gmres(c, gk, s, f2);
         S.krylov_its += gk.its;
         g.precs = gk.precs;
         g.jvs = gk.jvs;
@@ -1130,15 +1136,6 @@ static int solve_on(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             c->err = "GMRES stalled above its tolerance in consecutive Newton steps";
             return finish(BFS_ENOCONV);
         }
-        {
-            int fl = 0;
-            BFS_CUDA_TRY(c, cudaMemcpyAsync(&fl, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-            BFS_CUDA_TRY(c, cudaStreamSynchronize(s));
-            if (fl & 2) {
-                c->err = "a wait in the preconditioner sweeps timed out";
-                return finish(BFS_ETIMEOUT);
-            }
-        }
         double mu = 1.0;
         bool ok = false;
         while (mu >= 1e-4) {
@@ -1147,7 +1144,14 @@ static int solve_on(bfs_ctx *c, double *u, bfs_stats *st, cudaStream_t s)
             if ((rc = residual_launch(c, c->d_ut, c->d_Ft, cur, s))) return finish(rc);
             count(cur);
             norms_launch(c, c->d_Ft, n, c->d_scal + 12, c->d_scal + 13, s);
+            // the sweeps' timeout bit travels with the trial's norms (one round trip)
+            int *hflag = reinterpret_cast<int *>(c->h_pin + 3);
+            BFS_CUDA_TRY(c, cudaMemcpyAsync(hflag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
             if ((rc = read_scalars(c, c->d_scal + 12, 2, s))) return finish(rc);
+            if (*hflag & 2) {
+                c->err = "a wait in the preconditioner sweeps timed out";
+                return finish(BFS_ETIMEOUT);
+            }
             if (isfinite(c->h_pin[0]) && c->h_pin[0] <= (1.0 - 1e-4 * mu) * f2) {
                 ok = true;
                 break;
