@@ -161,6 +161,18 @@ def cpu_oracle_rate(mesh, topo, F, u, reps: int = 1):
     return mesh.pair_evals() / dt, O.num_threads(), dt
 
 
+def cpu_oracle_rate_one_thread(mesh, topo, F, u):
+    """The same oracle residual on one host thread (the thread count restored)."""
+    import oracle as O
+    n = O.num_threads()
+    O.set_threads(1)
+    try:
+        rate, _, dt = cpu_oracle_rate(mesh, topo, F, u, reps=1)
+    finally:
+        O.set_threads(n)
+    return rate, dt
+
+
 def run_reference(args):
     """The oracle on the host cores, same config, metric and unit."""
     import oracle as O
@@ -719,9 +731,11 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, cores, dt = cpu_oracle_rate(mesh, topo, F, W.smooth_guess(mesh, 7), reps=1)
+        rate1, dt1 = cpu_oracle_rate_one_thread(mesh, topo, F, W.smooth_guess(mesh, 7))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"one full FP64 oracle residual at 181x61 ({mesh.pair_evals():.3e} pair "
-                         f"evaluations, {dt:.2f} s)"}
+                         f"evaluations, {dt:.2f} s)",
+               "one_thread": {"value": rate1, "seconds": dt1}}
 
     # ---- the large configuration (361 x 121, 7.6e9 pair evaluations per
     # residual): residual throughput beside the oracle's, outside the timed region
