@@ -738,7 +738,10 @@ int gm_multi_post(bfs_ctx *const *cs, Gm *const *gs, int cnt, cudaStream_t s)
             g.jvs++;
             c->launches++;
         }
-        if (set.start[k] > cap) return BFS_ECUDA;  // cannot happen: target <= cap - k
+        if (set.start[k] > cap) {  // cannot happen: target <= cap - k
+            cs[o]->err = "multi-instance Arnoldi tail: more CTA groups than can be resident";
+            return BFS_ECUDA;
+        }
         void *args[] = {&set};
         BFS_CUDA_TRY(cs[o], cudaLaunchCooperativeKernel((const void *)k_marnoldi_tail, dim3(set.start[k]),
                                                         dim3(TAIL_TPB), args, 0, s));
