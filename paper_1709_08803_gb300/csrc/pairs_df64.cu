@@ -71,6 +71,36 @@ __device__ __forceinline__ df df_mulf(df a, float b)
     return fast_two_sum(p, e);
 }
 
+// The same three without the final renormalisation (the pair stays an exact
+// unevaluated sum, its low part up to about 2^-22 of the high one), for the
+// quantities of the pair sum that cannot cancel: sums of squares, powers of
+// 1/r, and products entering a renormalising accumulation.
+__device__ __forceinline__ df df_add_s(df a, df b)
+{
+    float s = a.hi + b.hi;
+    float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    return mk(s, e);
+}
+
+__device__ __forceinline__ df df_mul_s(df a, df b)
+{
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return mk(p, e);
+}
+
+__device__ __forceinline__ df df_sqr_s(df a)
+{
+    float p = a.hi * a.hi;
+    float e = fmaf(a.hi, a.hi, -p);
+    e = fmaf(2.0f * a.hi, a.lo, e);
+    return mk(p, e);
+}
+
 __device__ __forceinline__ df df_sqr(df a)
 {
     float p = a.hi * a.hi;
@@ -187,44 +217,44 @@ k_pairs_df(const float *__restrict__ src, int per_split, const float *__restrict
             // S2 at the top target
             {
                 const df q = df_add(df_add(df_mulf(A, sxx), df_mulf(Bry, sdj)), df_mulf(Cry2, djj));
-                aS = df_add(aS, df_mul(w2, df_rsqrt(q)));
+                aS = df_add(aS, df_mul_s(w2, df_rsqrt(q)));
             }
             // top target, top source
             {
                 const df d = df_sub(zs, tz);
-                const df ri = df_rsqrt(df_add(rho2, df_sqr(d)));
-                const df ri3 = df_mul(df_sqr(ri), ri);
+                const df ri = df_rsqrt(df_add_s(rho2, df_sqr_s(d)));
+                const df ri3 = df_mul_s(df_sqr_s(ri), ri);
                 const df num = df_sub(df_sub(d, df_mulf(zxs, sx)), df_mulf(zys, dj));
                 const df dens = df_sub(w1f, df_mul(tf, w1));
-                aT1 = df_add(aT1, df_mul(df_mul(dens, num), ri3));
-                aT2 = df_add(aT2, df_mul(w2zx, ri));
+                aT1 = df_add(aT1, df_mul_s(df_mul_s(dens, num), ri3));
+                aT2 = df_add(aT2, df_mul_s(w2zx, ri));
             }
             // top target, bottom source
             {
                 const df d = df_sub(bs, cTB);
-                const df ri = df_rsqrt(df_add(rho2, df_sqr(d)));
-                const df ri3 = df_mul(df_sqr(ri), ri);
+                const df ri = df_rsqrt(df_add_s(rho2, df_sqr_s(d)));
+                const df ri3 = df_mul_s(df_sqr_s(ri), ri);
                 const df num = df_sub(df_sub(d, df_mulf(bxs, sx)), df_mulf(bys, dj));
-                aT1 = df_sub(aT1, df_mul(df_mul(w1g, num), ri3));
-                aT2 = df_add(aT2, df_mul(w2sb, ri));
+                aT1 = df_sub(aT1, df_mul_s(df_mul_s(w1g, num), ri3));
+                aT2 = df_add(aT2, df_mul_s(w2sb, ri));
             }
             // bottom target, top source
             {
                 const df d = df_sub(zs, cBT);
-                const df ri = df_rsqrt(df_add(rho2, df_sqr(d)));
-                const df ri3 = df_mul(df_sqr(ri), ri);
+                const df ri = df_rsqrt(df_add_s(rho2, df_sqr_s(d)));
+                const df ri3 = df_mul_s(df_sqr_s(ri), ri);
                 const df num = df_sub(df_sub(d, df_mulf(zxs, sx)), df_mulf(zys, dj));
-                aB1 = df_add(aB1, df_mul(df_mul(w1f, num), ri3));
-                aB2 = df_add(aB2, df_mul(w2zx, ri));
+                aB1 = df_add(aB1, df_mul_s(df_mul_s(w1f, num), ri3));
+                aB2 = df_add(aB2, df_mul_s(w2zx, ri));
             }
             // bottom target, bottom source
             {
                 const df d = df_sub(bs, tB);
-                const df ri = df_rsqrt(df_add(rho2, df_sqr(d)));
-                const df ri3 = df_mul(df_sqr(ri), ri);
+                const df ri = df_rsqrt(df_add_s(rho2, df_sqr_s(d)));
+                const df ri3 = df_mul_s(df_sqr_s(ri), ri);
                 const df num = df_sub(df_sub(d, df_mulf(bxs, sx)), df_mulf(bys, dj));
                 const df dens = df_sub(w1g, df_mul(tg, w1));
-                aB1 = df_sub(aB1, df_mul(df_mul(dens, num), ri3));
+                aB1 = df_sub(aB1, df_mul_s(df_mul_s(dens, num), ri3));
             }
         }
     }

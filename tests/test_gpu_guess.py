@@ -49,12 +49,12 @@ def test_learned_guess_on_held_out_draws(net_and_draws):
     (the library's learned solve: the uniform stream only if the guess fails)
     on 100 held-out draws of the training distribution (F ~ U[0.5, 1.4],
     bumps or a ridge; most have no steady solution the solver reaches).
-    Measured with these weights: 9 draws converge from the uniform stream, 12
-    or 13 directly from the guess (the gains lie near F = 1); on the 8 that
-    converge from both, the guess needed 2306 Krylov iterations against 3218
-    in one build and 2532 against 2623 in the next (rounding-level changes to
-    the FP32C residual move GMRES paths on these draws by up to a fifth), and
-    54-55 Newton steps against 57-59.  Asserted: every draw that converges
+    Measured with these weights: 9 draws converge from the uniform stream,
+    11-13 directly from the guess (the gains lie near F = 1); on the 8 that
+    converge from both, the guess needed 2306 Krylov iterations against 3218,
+    2532 against 2623 and 2585 against 2953 in three successive builds
+    (rounding-level changes to the residuals move GMRES paths on these draws
+    by up to a fifth), and 54-55 Newton steps against 57-59.  Asserted: every draw that converges
     from the uniform stream converges in the learned solve; at least one more
     draw converges from the guess than from the uniform stream; and on the
     draws both reach, the guess needs no more Krylov iterations in total."""
