@@ -325,13 +325,85 @@ def run_large(log=print, with_plain: bool = True, with_learned: bool = True, max
     return rep
 
 
+def run_large_sequenced(log=print, half_band: int = 12, coarse_half_band: int = 6, max_newton: int = 25,
+                        max_krylov: int = 150, stages=(1.0 / 3.0, 2.0 / 3.0, 1.0)):
+    """Mesh sequencing for the large configuration.  At each bump height of
+    the continuation, Newton first runs on the same rectangle at twice the
+    spacing (dx = 0.4, 181 x 61), starting from the previous coarse stage.
+    It then runs on the 361 x 121 mesh, starting from the coarse solution
+    interpolated onto it (sequencing.interpolate_u), with the previous fine
+    stage as the fallback start.  The mixed form throughout; half_band slices
+    for the fine mesh's preconditioner (twice App. A's b = M/10, which the
+    fine mesh needs at F = 0.9).  Stops at the first stage that fails."""
+    import torch
+
+    from . import bfs
+    from . import surrogate as S
+    from . import workloads as W
+    from .sequencing import interpolate_u
+
+    mf, topo_f, F = W.config_large()
+    mc, topo_c, _ = W.config_large(2)
+
+    def opts(hb):
+        return bfs.default_options(tol=1e-8, eta=1e-2, forcing=1, half_band=hb, krylov_precision=bfs.BFS_FP32C,
+                                   outer_precision=bfs.BFS_DF64, refine_below=1e-5,
+                                   precond_precision=bfs.BFS_FP32C, max_newton=max_newton, max_krylov=max_krylov)
+
+    rep = {"case": "large_sequenced", "F": F, "fine": f"{mf.N}x{mf.M}", "coarse": f"{mc.N}x{mc.M}",
+           "half_band": half_band, "coarse_half_band": coarse_half_band, "max_newton": max_newton,
+           "max_krylov": max_krylov, "stages": []}
+    cc = bfs.Context(mc, topo_c, F, opts(coarse_half_band))
+    cf = bfs.Context(mf, topo_f, F, opts(half_band))
+    for name, c in (("coarse", cc), ("fine", cf)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        c.precond_factor()
+        torch.cuda.synchronize()
+        rep[f"factor_s_{name}"] = time.perf_counter() - t
+
+    def solve(c, u):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st = c.solve(u, raise_on_error=False)
+        torch.cuda.synchronize()
+        z = c.unpack(u)["zeta"]
+        return {"status": st["status"], "newton": st["newton_its"], "krylov": st["krylov_its"],
+                "fnorm_inf": st["fnorm_inf"], "zeta_max": float(z.max()), "zeta_min": float(z.min()),
+                "seconds": time.perf_counter() - t}
+
+    uc, uf_prev = cc.flat_guess(), None
+    for s in stages:
+        rec = {"scale": s}
+        rep["stages"].append(rec)
+        cc.set_topography(S.scaled(topo_c, s))
+        cf.set_topography(S.scaled(topo_f, s))
+        rec["coarse"] = solve(cc, uc)
+        log(json.dumps(rec))
+        if rec["coarse"]["status"] != 0:
+            break
+        uf = torch.tensor(interpolate_u(mc, uc.cpu().numpy(), mf), device="cuda")
+        rec["fine_from_coarse"] = solve(cf, uf)
+        if rec["fine_from_coarse"]["status"] != 0 and uf_prev is not None:
+            uf = uf_prev.clone()
+            rec["fine_from_previous"] = solve(cf, uf)
+        log(json.dumps(rec))
+        if rec.get("fine_from_previous", rec["fine_from_coarse"])["status"] != 0:
+            break
+        uf_prev = uf
+    cc.close()
+    cf.close()
+    return rep
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="super", choices=["super", "sub", "compare", "large"],
                     help="compare: bump vs equivalent pressure at eps = the first --eps (Sec. 6)")
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1, 0.5, 1.0, 1.5, 2.0, 2.5, 2.75])
     ap.add_argument("--F", type=float, default=None, help="Froude number of the supercritical case (3)")
-    ap.add_argument("--half-band", type=int, default=3)
+    ap.add_argument("--half-band", type=int, default=None,
+                    help="preconditioner half band in slices (3; 12 for --sequence)")
     ap.add_argument("--max-newton", type=int, default=40)
     ap.add_argument("--max-krylov", type=int, default=400)
     ap.add_argument("--tol", type=float, default=1e-8,
@@ -342,11 +414,15 @@ def main(argv=None):
     ap.add_argument("--start-u", default=None, help="start from a --save-u file instead of the uniform stream")
     ap.add_argument("--no-secant", action="store_true", help="start each stage from the previous solution only")
     ap.add_argument("--no-plain", action="store_true", help="large case: skip the plain FP64 solve")
+    ap.add_argument("--sequence", action="store_true",
+                    help="large case: mesh sequencing from dx = 0.4 at each continuation stage")
     ap.add_argument("--out", default=None, help="report (JSON), rewritten after every stage")
     ap.add_argument("--fields", default=None, help="surface fields of every converged stage (.npz)")
     ap.add_argument("--analyse", default=None,
                     help="recompute the wake metrics from a --fields file of a supercritical run (no GPU)")
     a = ap.parse_args(argv)
+    if a.half_band is None and not (a.case == "large" and a.sequence):
+        a.half_band = 3
     if a.analyse:
         from . import workloads as W
         mesh, _, _ = W.config_supercritical_281(0.1, 3.0 if a.F is None else a.F)
@@ -358,6 +434,15 @@ def main(argv=None):
     import __graft_entry__
     __graft_entry__.build()
     saved = {}
+    if a.case == "large" and a.sequence:
+        rep = run_large_sequenced(log=lambda m: print(m, file=sys.stderr, flush=True),
+                                  half_band=12 if a.half_band is None else a.half_band,
+                                  max_newton=a.max_newton, max_krylov=a.max_krylov)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(rep, fh, indent=1)
+        print(json.dumps(rep))
+        return 0
     if a.case == "large":
         rep = run_large(log=lambda m: print(m, file=sys.stderr, flush=True), max_newton=a.max_newton,
                         max_krylov=a.max_krylov, with_plain=not a.no_plain)

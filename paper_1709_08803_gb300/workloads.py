@@ -151,13 +151,17 @@ def config_paper_scale(F: float = 0.7):
     return mesh, topo, F
 
 
-def config_large():
+def config_large(coarsen: int = 1):
     """361x121 full mesh, dx = dy = 0.2, x in [-20, 52], y in [-12, 12], F = 0.9,
     bump 0.3 exp(-(x^2 + y^2)) plus a cross-stream ridge 0.005 exp(-(x-5)^2 / 2).
     The ridge height is not given; a two-dimensional ridge blocks steady
     subcritical flow above the hydraulic critical height 1 + F^2/2 - (3/2) F^(2/3)
-    of the depth (0.0067 at F = 0.9), so it is taken below that."""
-    mesh = Mesh(N=361, M=121, x1=-20.0, y1=-12.0, dx=0.2, dy=0.2, half=0)
+    of the depth (0.0067 at F = 0.9), so it is taken below that.
+    coarsen = c: the same rectangle and bottom at spacing 0.2 c (c divides 120)."""
+    if coarsen < 1 or 120 % coarsen:
+        raise ValueError("coarsen must divide 120")
+    mesh = Mesh(N=360 // coarsen + 1, M=120 // coarsen + 1, x1=-20.0, y1=-12.0, dx=0.2 * coarsen,
+                dy=0.2 * coarsen, half=0)
     topo = gaussian_bumps(mesh, [(0.3, 1.0 / math.sqrt(2.0), 0.0, 0.0)], ridges=[(0.005, 1.0, 5.0)])
     return mesh, topo, 0.9
 
